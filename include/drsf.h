@@ -1,0 +1,200 @@
+/*
+ * drsf.h -- C ABI of the GB300 (sm_103a) dynamic rooted spanning forest
+ * library.
+ *
+ * The library maintains a rooted spanning forest F of an undirected graph G
+ * on one GPU under batches of edge insertions or deletions: the Dynamic
+ * Rooted Spanning Forest (D-RSF) problem of Sahu, Singh, Nandy and
+ * Ramakrishna, "Fully Dynamic Rooted Spanning Tree on GPU" (problem box,
+ * Section I).  Input: G, a rooted spanning forest F of G, a batch B and an
+ * operation op; output: a rooted spanning forest F' of G' = G + B (insert)
+ * or G - B (delete).  The update follows Algorithm 1 (Section II): update
+ * the graph, cut deleted tree edges, label every vertex with its tree root
+ * by pointer jumping, find replacement edges among the cross edges by
+ * hooking and compressing (Section III-B, Algorithm 2), orient them by an
+ * Euler tour of the tree-of-trees (Section I preliminaries), then reverse
+ * the affected root paths in parallel and attach (Algorithm 1, Section
+ * III-C/D).
+ *
+ * Conventions
+ *   - Vertex ids are int32 in [0, n); n <= 2^31 - 1.
+ *   - Edges and batches are arrays of int32 pairs (u, v), row-major, i.e.
+ *     element 2*i is u_i and 2*i+1 is v_i.  Edges are undirected.
+ *   - parent[v] == v marks a root.
+ *   - Pointers documented "device" must be CUDA device (or managed) memory
+ *     readable by the stream's device; "host" pointers are ordinary or
+ *     pinned host memory.
+ *   - Every call is ordered on the given stream.  Calls on one handle must
+ *     not overlap on different streams.
+ *   - The caller owns all buffers it passes in; the library copies what it
+ *     needs and never keeps caller pointers.  All library memory comes from
+ *     the allocator registered with drsf_set_allocator (default cudaMalloc /
+ *     cudaFree).
+ *
+ * Errors
+ *   Every call returns a drsf_status.  drsf_apply checks its arguments on
+ *   the host and returns without a host synchronisation; errors detected on
+ *   the device (an out-of-range vertex id in a batch, a bounded wait that
+ *   timed out) are latched in the handle and reported by the next
+ *   drsf_stats / drsf_sync call (drsf_parent and drsf_labels only enqueue
+ *   work and report a handle already known to be poisoned).  A batch with
+ *   an out-of-range id is not applied at all (DRSF_EINVAL is reported once).
+ *   A timeout or internal capacity fault poisons the handle
+ *   (DRSF_EPOISONED from then on); destroy it.
+ */
+#ifndef DRSF_H
+#define DRSF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DRSF_API __attribute__((visibility("default")))
+#else
+#define DRSF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct drsf_ctx *drsf_handle;
+/* A cudaStream_t, passed as an opaque pointer so that this header does not
+ * need the CUDA headers.  NULL is the legacy default stream. */
+typedef void *drsf_stream;
+
+typedef enum {
+    DRSF_OK = 0,
+    DRSF_EINVAL = 1,      /* bad argument or out-of-range vertex id */
+    DRSF_ENOMEM = 2,      /* allocation failed; the handle is unchanged */
+    DRSF_ECUDA = 3,       /* a CUDA runtime call failed */
+    DRSF_ENOT_FOREST = 4, /* DRSF_VALIDATE: parent is not a rooted spanning forest of G */
+    DRSF_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
+    DRSF_EPOISONED = 6    /* an earlier device fault left the handle unusable */
+} drsf_status;
+
+typedef enum { DRSF_INSERT = 0, DRSF_DELETE = 1 } drsf_op;
+
+enum {
+    /* Minimum-key replacement edges and smallest-root-id super-roots: the
+     * result is a function of the inputs alone (bit-identical parent arrays
+     * run to run).  Always on in this version; accepted for compatibility. */
+    DRSF_DETERMINISTIC = 1u,
+    /* drsf_create checks on the device that parent is a rooted spanning
+     * forest of G and fails with DRSF_ENOT_FOREST otherwise (synchronises). */
+    DRSF_VALIDATE = 2u
+};
+
+/* Per-batch counters of the last applied batch (drsf_stats). */
+typedef struct {
+    int64_t batch_len;     /* |B| as passed */
+    int64_t self_loops;    /* dropped: u == v */
+    int64_t dropped;       /* dropped: duplicate in B, or insert of an existing /
+                              delete of an absent edge */
+    int64_t applied;       /* edges actually inserted / deleted */
+    int64_t tree_cut;      /* deleted edges that were tree edges (delete) */
+    int64_t affected;      /* vertices of trees that lost an edge (delete) */
+    int64_t detached;      /* vertices whose tree root changed after the cut */
+    int64_t scanned;       /* adjacency entries scanned for cross edges */
+    int64_t candidates;    /* cross edges found */
+    int64_t hook_rounds;   /* hook-and-compress rounds */
+    int64_t replacement;   /* replacement edges |E_r| */
+    int64_t rank_rounds;   /* list-ranking rounds of the Euler tour */
+    int64_t active;        /* vertices in re-rooted trees (path reversal) */
+    int64_t reversed;      /* vertices whose parent pointer was reversed */
+    int64_t mark_rounds;   /* pointer-doubling rounds of the path reversal */
+    int64_t jump_rounds;   /* pointer-jumping rounds for representatives */
+    int64_t edges;         /* |E(G')| after the batch */
+    int64_t overflow;      /* edges held outside their CSR row (slack exhausted) */
+    int64_t rebuilds;      /* CSR / index rebuilds so far */
+} drsf_batch_stats;
+
+/* Allocator hooks.  alloc(bytes, stream, ctx) returns device memory or NULL;
+ * free(ptr, stream, ctx) releases it.  Pass NULLs to restore cudaMalloc /
+ * cudaFree.  Affects handles created afterwards.  Not thread-safe. */
+typedef void *(*drsf_alloc_fn)(size_t bytes, drsf_stream stream, void *ctx);
+typedef void (*drsf_free_fn)(void *ptr, drsf_stream stream, void *ctx);
+DRSF_API drsf_status drsf_set_allocator(drsf_alloc_fn alloc, drsf_free_fn free_fn, void *ctx);
+
+/*
+ * drsf_create -- build the device state for G and F (problem box, Section I:
+ * "an undirected graph G and a rooted spanning forest F of G").
+ *   n       number of vertices, 1 <= n <= 2^31 - 1
+ *   edges   device, int32[2*m], the edge list of G; self-loops and repeated
+ *           pairs are dropped; m may be 0 (edges may then be NULL)
+ *   parent  device, int32[n], F as parent pointers (parent[r] == r at roots)
+ *   flags   DRSF_DETERMINISTIC | DRSF_VALIDATE
+ *   out     receives the handle (NULL on failure)
+ * The graph is stored as a slack CSR (int64 row offsets, int32 columns) with
+ * an open-addressing edge index for O(1) deletion.  Synchronises the stream
+ * once (to size the CSR).  Without DRSF_VALIDATE, an F that is not a rooted
+ * spanning forest of G gives undefined (but memory-safe) results.
+ * Errors: DRSF_EINVAL (n out of range, negative m, NULL pointers, an id out
+ * of range), DRSF_ENOMEM, DRSF_ECUDA, DRSF_ENOT_FOREST.
+ */
+DRSF_API drsf_status drsf_create(int32_t n, const int32_t *edges, int64_t m, const int32_t *parent,
+                        uint32_t flags, drsf_stream stream, drsf_handle *out);
+
+/*
+ * drsf_apply -- apply one batch (Algorithm 1, Section II-D).
+ *   op     DRSF_INSERT (G' = G + B) or DRSF_DELETE (G' = G - B)
+ *   batch  device, int32[2*len], the batch B as (u, v) pairs; len may be 0
+ * Normalisation: self-loops, pairs repeated within B, insertion of an edge
+ * already in G and deletion of an edge not in G are dropped and counted.
+ * Asynchronous: returns once the work is enqueued on `stream`; no host
+ * synchronisation unless the graph storage must grow (slack or index
+ * exhausted), which the host detects from conservative bounds.
+ * Errors (immediate): DRSF_EINVAL (bad op, negative len, NULL batch with
+ * len > 0), DRSF_ENOMEM, DRSF_ECUDA, DRSF_EPOISONED.  An out-of-range id is
+ * reported later as DRSF_EINVAL and the batch is skipped.
+ */
+DRSF_API drsf_status drsf_apply(drsf_handle h, drsf_op op, const int32_t *batch, int64_t len, drsf_stream stream);
+
+/*
+ * drsf_apply_host -- as drsf_apply, with `batch` in host memory (pinned for
+ * a truly asynchronous copy).  The library stages it to the device on
+ * `stream` before the update.  The host buffer may be reused once this call
+ * returns (the library copies through its own pinned staging buffer).
+ */
+DRSF_API drsf_status drsf_apply_host(drsf_handle h, drsf_op op, const int32_t *batch, int64_t len,
+                            drsf_stream stream);
+
+/* drsf_parent -- copy F' (int32[n], parent[r] == r at roots) to device
+ * buffer `out` on `stream`.  Does not synchronise. */
+DRSF_API drsf_status drsf_parent(drsf_handle h, int32_t *out, drsf_stream stream);
+
+/*
+ * drsf_labels -- connected-component labels of G' (connectivity maintenance,
+ * Section I contributions): out[v] = smallest vertex id of v's component,
+ * written to device buffer int32[n] on `stream`.  Every tree of F' spans one
+ * component, so the label is the minimum over v's tree.
+ */
+DRSF_API drsf_status drsf_labels(drsf_handle h, int32_t *out, drsf_stream stream);
+
+/* drsf_stats -- counters of the last batch; synchronises `stream`; returns
+ * any latched device error. */
+DRSF_API drsf_status drsf_stats(drsf_handle h, drsf_batch_stats *out, drsf_stream stream);
+
+/* drsf_sync -- synchronise `stream` and return any latched device error. */
+DRSF_API drsf_status drsf_sync(drsf_handle h, drsf_stream stream);
+
+/* drsf_num_vertices / drsf_num_edges -- sizes (num_edges synchronises). */
+DRSF_API int32_t drsf_num_vertices(drsf_handle h);
+DRSF_API int64_t drsf_num_edges(drsf_handle h, drsf_stream stream);
+
+/* drsf_export_edges -- write the edge list of G' (int32[2*m], u < v per
+ * pair, unspecified order) into device buffer `out` of capacity `cap` pairs;
+ * *m_out receives the number of edges.  Synchronises. */
+DRSF_API drsf_status drsf_export_edges(drsf_handle h, int32_t *out, int64_t cap, int64_t *m_out, drsf_stream stream);
+
+/* drsf_destroy -- release all device memory (synchronises the handle's last
+ * stream).  NULL is a no-op. */
+DRSF_API void drsf_destroy(drsf_handle h);
+
+/* drsf_error_string -- static description of a status. */
+DRSF_API const char *drsf_error_string(drsf_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DRSF_H */

@@ -1,0 +1,712 @@
+// Host side of the D-RSF library: handle lifetime, graph storage build and
+// rebuild, the per-batch launch sequence (Algorithm 1) and the C ABI of
+// include/drsf.h.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "kernels.h"
+
+namespace {
+
+drsf_alloc_fn g_alloc = nullptr;
+drsf_free_fn g_free = nullptr;
+void *g_alloc_ctx = nullptr;
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct drsf_ctx {
+    int n = 0;
+    uint32_t flags = 0;
+    int device = 0;
+    Dev dev{};
+    drsf_alloc_fn alloc = nullptr;
+    drsf_free_fn dfree = nullptr;
+    void *alloc_ctx = nullptr;
+    std::vector<Buf> bufs;
+    bool poisoned = false;
+    int pending_einval = 0;
+
+    Ctl *ctl = nullptr;
+    Ctl *ctl_host = nullptr;   // pinned
+
+    // forest
+    int *parent = nullptr, *rep = nullptr;
+    // graph
+    long long *off = nullptr;
+    int *used = nullptr, *col = nullptr;
+    long long col_cap = 0;
+    Index ix{};
+    u64 H = 0;
+    u64 *ovf = nullptr;
+    u64 ovf_cap = 0;
+    // n-sized work arrays
+    int *J0 = nullptr, *J1 = nullptr, *comp = nullptr, *minp = nullptr, *pidx = nullptr, *plist = nullptr;
+    int *att_x = nullptr, *newrep = nullptr, *A = nullptr, *act = nullptr, *pold = nullptr, *D = nullptr;
+    int *chx = nullptr, *chy = nullptr;
+    unsigned *aff_ep = nullptr, *cut_ep = nullptr, *pstamp = nullptr, *att_ep = nullptr, *rep_ep = nullptr;
+    u64 *best0 = nullptr, *best1 = nullptr, *er = nullptr;
+    unsigned char *mark = nullptr;
+    int *pdeg = nullptr, *pcur = nullptr, *poff = nullptr, *adj = nullptr, *apos = nullptr;
+    int *val0 = nullptr, *val1 = nullptr, *nx0 = nullptr, *nx1 = nullptr;
+    long long *bsum = nullptr;
+    // candidates
+    u64 *ck[2] = {nullptr, nullptr};
+    int *ca[2] = {nullptr, nullptr}, *cb[2] = {nullptr, nullptr};
+    u64 cand_cap = 0;
+    // batch work
+    u64 *nkey = nullptr, *nslot = nullptr;
+    int *cutlist = nullptr;
+    long long batch_cap = 0;
+    int *stage_dev = nullptr;
+    int *stage_host = nullptr;   // pinned
+    long long stage_cap = 0;
+    cudaEvent_t stage_done = nullptr;
+    bool stage_pending = false;
+    // host-side bounds that decide a storage rebuild without a device read
+    long long occ_bound = 0;     // index slots in use (live + deleted)
+    long long ovf_bound = 0;     // overflow entries
+    long long ctomb_bound = 0;   // deleted CSR entries
+    long long rebuilds = 0;
+};
+
+// ------------------------------------------------------------- memory
+
+static void *raw_alloc(drsf_ctx *h, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (h->alloc) {
+        p = h->alloc(bytes, (drsf_stream)s, h->alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+static void raw_free(drsf_ctx *h, void *p, cudaStream_t s) {
+    if (!p) return;
+    if (h->dfree) h->dfree(p, (drsf_stream)s, h->alloc_ctx);
+    else cudaFree(p);
+}
+
+template <class T>
+static bool halloc(drsf_ctx *h, T **out, size_t count, cudaStream_t s) {
+    void *p = raw_alloc(h, count * sizeof(T), s);
+    if (!p) return false;
+    h->bufs.push_back({p, count * sizeof(T)});
+    *out = (T *)p;
+    return true;
+}
+
+template <class T>
+static void hfree(drsf_ctx *h, T **ptr, cudaStream_t s) {
+    if (!*ptr) return;
+    for (size_t i = 0; i < h->bufs.size(); ++i)
+        if (h->bufs[i].p == (void *)*ptr) {
+            h->bufs.erase(h->bufs.begin() + (long)i);
+            break;
+        }
+    raw_free(h, (void *)*ptr, s);
+    *ptr = nullptr;
+}
+
+#define CK(x)                                     \
+    do {                                          \
+        cudaError_t e_ = (x);                     \
+        if (e_ != cudaSuccess) {                  \
+            cudaGetLastError();                   \
+            return DRSF_ECUDA;                    \
+        }                                         \
+    } while (0)
+#define CKA(x)                                    \
+    do {                                          \
+        if (!(x)) return DRSF_ENOMEM;             \
+    } while (0)
+
+static u64 pow2_at_least(u64 x) {
+    u64 p = 1024;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// ------------------------------------------------------------ storage
+
+// Build the slack CSR, the edge index and the overflow list from an edge
+// list on the device (create and rebuild).  Synchronises `s`.
+static drsf_status build_graph(drsf_ctx *h, const int *edges, long long m, cudaStream_t s, long long *m_out,
+                               long long *self_loops_out) {
+    const int n = h->n;
+    // index sized for load <= 0.5 with headroom for insertions
+    long long headroom = std::max<long long>(m / 2, 1 << 16);
+    u64 H = pow2_at_least((u64)(2 * (m + headroom)));
+    Index ix{};
+    CKA(halloc(h, &ix.key, H, s));
+    CKA(halloc(h, &ix.pu, H, s));
+    CKA(halloc(h, &ix.pv, H, s));
+    ix.mask = H - 1;
+    CK(cudaMemsetAsync(ix.key, 0xFF, H * sizeof(u64), s));
+
+    u64 *dkey = nullptr, *dslot = nullptr, *cnt = nullptr;
+    long long *tmp64 = nullptr, *bs = nullptr;
+    int *deg = nullptr;
+    CKA(halloc(h, &dkey, (size_t)std::max<long long>(m, 1), s));
+    CKA(halloc(h, &dslot, (size_t)std::max<long long>(m, 1), s));
+    CKA(halloc(h, &cnt, 4, s));
+    CKA(halloc(h, &deg, (size_t)n, s));
+    CKA(halloc(h, &tmp64, (size_t)n + 1, s));
+    long long tiles = ((long long)n + 4095) / 4096 + 1;
+    CKA(halloc(h, &bs, (size_t)tiles, s));
+    CK(cudaMemsetAsync(cnt, 0, 4 * sizeof(u64), s));
+    CK(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(int), s));
+    if (m > 0) CK(launch_create_claim(edges, m, ix, dkey, dslot, cnt, (long long *)(cnt + 1), s));
+    u64 hc[2] = {0, 0};
+    CK(cudaMemcpyAsync(hc, cnt, 2 * sizeof(u64), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    long long m2 = (long long)hc[0];
+    CK(launch_degree(dkey, m2, deg, s));
+    CK(launch_caps(deg, n, tmp64, s));
+    long long *off = nullptr;
+    CKA(halloc(h, &off, (size_t)n + 1, s));
+    CK(launch_scan_i64(tmp64, off, n, bs, s));
+    long long total = 0;
+    CK(cudaMemcpyAsync(&total, off + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (total >= (long long)POS_OVF - 1) return DRSF_ENOMEM;   // positions are 32-bit
+    int *col = nullptr, *used = nullptr;
+    CKA(halloc(h, &col, (size_t)total, s));
+    CKA(halloc(h, &used, (size_t)n, s));
+    CK(cudaMemsetAsync(col, 0xFF, (size_t)total * sizeof(int), s));
+    CK(cudaMemsetAsync(used, 0, (size_t)n * sizeof(int), s));
+    Csr g{off, used, col};
+    CK(launch_fill(dkey, dslot, m2, g, ix, s));
+    u64 ovf_cap = std::max<u64>(1u << 20, (u64)m2 / 16);
+    u64 *ovf = nullptr;
+    CKA(halloc(h, &ovf, ovf_cap, s));
+    // candidate buffers: every live undirected edge at most once
+    u64 need = (u64)total / 2 + ovf_cap + 1024;
+    if (need > h->cand_cap) {
+        for (int b = 0; b < 2; ++b) {
+            hfree(h, &h->ck[b], s);
+            hfree(h, &h->ca[b], s);
+            hfree(h, &h->cb[b], s);
+        }
+        for (int b = 0; b < 2; ++b) {
+            CKA(halloc(h, &h->ck[b], need, s));
+            CKA(halloc(h, &h->ca[b], need, s));
+            CKA(halloc(h, &h->cb[b], need, s));
+        }
+        h->cand_cap = need;
+    }
+    CK(cudaStreamSynchronize(s));
+    // swap in
+    hfree(h, &h->ix.key, s);
+    hfree(h, &h->ix.pu, s);
+    hfree(h, &h->ix.pv, s);
+    hfree(h, &h->off, s);
+    hfree(h, &h->col, s);
+    hfree(h, &h->used, s);
+    hfree(h, &h->ovf, s);
+    h->ix = ix;
+    h->H = H;
+    h->off = off;
+    h->col = col;
+    h->used = used;
+    h->col_cap = total;
+    h->ovf = ovf;
+    h->ovf_cap = ovf_cap;
+    hfree(h, &dkey, s);
+    hfree(h, &dslot, s);
+    hfree(h, &cnt, s);
+    hfree(h, &deg, s);
+    hfree(h, &tmp64, s);
+    hfree(h, &bs, s);
+    h->occ_bound = m2;
+    h->ovf_bound = 0;
+    h->ctomb_bound = 0;
+    *m_out = m2;
+    if (self_loops_out) *self_loops_out = (long long)hc[1];
+    return DRSF_OK;
+}
+
+static drsf_status ensure_batch(drsf_ctx *h, long long len, cudaStream_t s) {
+    if (len <= h->batch_cap) return DRSF_OK;
+    long long cap = std::max<long long>(len, 1 << 16);
+    CK(cudaStreamSynchronize(s));
+    hfree(h, &h->nkey, s);
+    hfree(h, &h->nslot, s);
+    hfree(h, &h->cutlist, s);
+    CKA(halloc(h, &h->nkey, (size_t)cap, s));
+    CKA(halloc(h, &h->nslot, (size_t)cap, s));
+    CKA(halloc(h, &h->cutlist, (size_t)cap, s));
+    h->batch_cap = cap;
+    return DRSF_OK;
+}
+
+static drsf_status read_ctl(drsf_ctx *h, cudaStream_t s) {
+    CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return DRSF_OK;
+}
+
+// Extract the live edge list and rebuild CSR + index + overflow (compacts
+// deleted entries, absorbs overflow edges, resizes the index).
+static drsf_status rebuild(drsf_ctx *h, cudaStream_t s) {
+    drsf_status st = read_ctl(h, s);
+    if (st) return st;
+    long long live = h->ctl_host->edges;
+    int *tmp = nullptr;
+    u64 *cnt = nullptr;
+    CKA(halloc(h, &tmp, (size_t)std::max<long long>(2 * live, 2), s));
+    CKA(halloc(h, &cnt, 2, s));
+    CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(u64), s));
+    Csr g{h->off, h->used, h->col};
+    CK(launch_extract(h->dev, h->n, g, h->ovf, h->ovf_cap, h->ctl, tmp, live, cnt, s));
+    u64 hc[2];
+    CK(cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if ((long long)hc[0] != live || ((int *)hc)[2] != 0) {
+        h->poisoned = true;
+        return DRSF_EPOISONED;
+    }
+    long long m2 = 0;
+    st = build_graph(h, tmp, live, s, &m2, nullptr);
+    hfree(h, &tmp, s);
+    hfree(h, &cnt, s);
+    if (st) return st;
+    // reset the storage counters of the control block
+    Ctl c = *h->ctl_host;
+    c.ovf_count = 0;
+    c.edges = m2;
+    c.htomb = 0;
+    c.ctomb = 0;
+    CK(cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    h->rebuilds++;
+    return DRSF_OK;
+}
+
+// Decide from host-side bounds whether the storage could run out during a
+// batch of `len`; only then read the real counts (one synchronisation) and
+// rebuild if needed.
+static drsf_status storage_check(drsf_ctx *h, int op, long long len, cudaStream_t s) {
+    if (op == DRSF_INSERT) {
+        bool maybe = h->occ_bound + len > (long long)(0.7 * (double)h->H) ||
+                     h->ovf_bound + len > (long long)h->ovf_cap;
+        if (maybe) {
+            drsf_status st = read_ctl(h, s);
+            if (st) return st;
+            long long occ = h->ctl_host->edges + h->ctl_host->htomb;
+            long long ovfc = (long long)h->ctl_host->ovf_count;
+            h->occ_bound = occ;
+            h->ovf_bound = ovfc;
+            if (occ + len > (long long)(0.7 * (double)h->H) || ovfc + len > (long long)h->ovf_cap) {
+                st = rebuild(h, s);
+                if (st) return st;
+            }
+        }
+        h->occ_bound += len;
+        h->ovf_bound += len;
+    } else {
+        h->ctomb_bound += 2 * len;
+        if (h->ctomb_bound > h->col_cap / 4) {
+            drsf_status st = read_ctl(h, s);
+            if (st) return st;
+            // deleted CSR entries = 2 * (deleted edges) - bounded by the
+            // index tombstones (each deleted edge frees two CSR entries)
+            long long ct = 2 * h->ctl_host->htomb + h->ctl_host->ctomb;
+            h->ctomb_bound = ct;
+            if (ct > h->col_cap / 4) {
+                st = rebuild(h, s);
+                if (st) return st;
+            }
+        }
+    }
+    return DRSF_OK;
+}
+
+static void set_dev(drsf_ctx *h) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != h->device) cudaSetDevice(h->device);
+}
+
+// -------------------------------------------------------------- create
+
+static drsf_status alloc_work(drsf_ctx *h, cudaStream_t s) {
+    size_t n = (size_t)h->n;
+    CKA(halloc(h, &h->parent, n, s));
+    CKA(halloc(h, &h->rep, n, s));
+    CKA(halloc(h, &h->J0, n, s));
+    CKA(halloc(h, &h->J1, n, s));
+    CKA(halloc(h, &h->comp, n, s));
+    CKA(halloc(h, &h->minp, n, s));
+    CKA(halloc(h, &h->pidx, n, s));
+    CKA(halloc(h, &h->plist, n + 1, s));
+    CKA(halloc(h, &h->att_x, n, s));
+    CKA(halloc(h, &h->newrep, n, s));
+    CKA(halloc(h, &h->A, n, s));
+    CKA(halloc(h, &h->act, n, s));
+    CKA(halloc(h, &h->pold, n, s));
+    CKA(halloc(h, &h->D, n, s));
+    CKA(halloc(h, &h->chx, n, s));
+    CKA(halloc(h, &h->chy, n, s));
+    CKA(halloc(h, &h->aff_ep, n, s));
+    CKA(halloc(h, &h->cut_ep, n, s));
+    CKA(halloc(h, &h->pstamp, n, s));
+    CKA(halloc(h, &h->att_ep, n, s));
+    CKA(halloc(h, &h->rep_ep, n, s));
+    CKA(halloc(h, &h->best0, n, s));
+    CKA(halloc(h, &h->best1, n, s));
+    CKA(halloc(h, &h->er, n, s));
+    CKA(halloc(h, &h->mark, n, s));
+    CKA(halloc(h, &h->pdeg, n + 1, s));
+    CKA(halloc(h, &h->pcur, n + 1, s));
+    CKA(halloc(h, &h->poff, n + 1, s));
+    CKA(halloc(h, &h->adj, 2 * n + 2, s));
+    CKA(halloc(h, &h->apos, 2 * n + 2, s));
+    CKA(halloc(h, &h->val0, 2 * n + 2, s));
+    CKA(halloc(h, &h->val1, 2 * n + 2, s));
+    CKA(halloc(h, &h->nx0, 2 * n + 2, s));
+    CKA(halloc(h, &h->nx1, 2 * n + 2, s));
+    CKA(halloc(h, &h->bsum, 8192, s));
+    CKA(halloc(h, &h->ctl, 1, s));
+    unsigned *eps[] = {h->aff_ep, h->cut_ep, h->pstamp, h->att_ep, h->rep_ep};
+    for (unsigned *e : eps) CK(cudaMemsetAsync(e, 0, n * sizeof(unsigned), s));
+    CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
+    return DRSF_OK;
+}
+
+static void destroy_all(drsf_ctx *h) {
+    if (!h) return;
+    set_dev(h);
+    cudaDeviceSynchronize();
+    for (auto &b : h->bufs) raw_free(h, b.p, nullptr);
+    h->bufs.clear();
+    if (h->ctl_host) cudaFreeHost(h->ctl_host);
+    if (h->stage_host) cudaFreeHost(h->stage_host);
+    if (h->stage_done) cudaEventDestroy(h->stage_done);
+    delete h;
+}
+
+extern "C" {
+
+drsf_status drsf_set_allocator(drsf_alloc_fn alloc, drsf_free_fn free_fn, void *ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) return DRSF_EINVAL;
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_ctx = ctx;
+    return DRSF_OK;
+}
+
+static drsf_status create_impl(drsf_ctx *h, const int32_t *edges, int64_t m, const int32_t *parent,
+                               cudaStream_t s) {
+    const int n = h->n;
+    drsf_status st = alloc_work(h, s);
+    if (st) return st;
+    st = ensure_batch(h, 1, s);
+    if (st) return st;
+    CK(cudaMallocHost((void **)&h->ctl_host, sizeof(Ctl)));
+    int *bad = nullptr;
+    CKA(halloc(h, &bad, 4, s));
+    CK(cudaMemsetAsync(bad, 0, 4 * sizeof(int), s));
+    if (m > 0) CK(launch_check_range(edges, 2 * m, n, bad, s));
+    CK(launch_check_range(parent, n, n, bad + 1, s));
+    int hb[2] = {0, 0};
+    CK(cudaMemcpyAsync(hb, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hb[0] || hb[1]) return DRSF_EINVAL;
+    long long m2 = 0, loops = 0;
+    st = build_graph(h, edges, m, s, &m2, &loops);
+    if (st) return st;
+    CK(cudaMemcpyAsync(h->parent, parent, (size_t)n * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    // representatives of F by pointer jumping over all vertices
+    CK(launch_copy_parent(n, h->parent, h->J0, s));
+    CK(launch_jump(h->dev, nullptr, 0, n, h->ctl, h->J0, h->J1, h->rep, h->D, 0, s));
+    Ctl c{};
+    CK(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (c.err & ERR_ROUNDS) return DRSF_ENOT_FOREST;   // pointers did not converge: a cycle
+    if (c.err & ERR_TIMEOUT) return DRSF_ETIMEOUT;
+    if (h->flags & DRSF_VALIDATE) {
+        CK(cudaMemsetAsync(bad, 0, 4 * sizeof(int), s));
+        CK(launch_check_tree_edges(n, h->parent, h->ix, bad, s));
+        // every live edge must join two vertices of the same tree
+        int *el = nullptr;
+        u64 *cnt = nullptr;
+        CKA(halloc(h, &el, (size_t)std::max<long long>(2 * m2, 2), s));
+        CKA(halloc(h, &cnt, 2, s));
+        CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(u64), s));
+        Csr g{h->off, h->used, h->col};
+        CK(launch_extract(h->dev, n, g, h->ovf, h->ovf_cap, h->ctl, el, m2, cnt, s));
+        CK(launch_check_cross(el, m2, h->rep, bad, s));
+        CK(cudaMemcpyAsync(hb, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        hfree(h, &el, s);
+        hfree(h, &cnt, s);
+        if (hb[0]) return DRSF_ENOT_FOREST;
+    }
+    hfree(h, &bad, s);
+    c.edges = m2;
+    c.self_loops = loops;
+    CK(cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return DRSF_OK;
+}
+
+drsf_status drsf_create(int32_t n, const int32_t *edges, int64_t m, const int32_t *parent, uint32_t flags,
+                        drsf_stream stream, drsf_handle *out) {
+    if (!out) return DRSF_EINVAL;
+    *out = nullptr;
+    if (n < 1 || m < 0 || !parent || (m > 0 && !edges)) return DRSF_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    drsf_ctx *h = new (std::nothrow) drsf_ctx();
+    if (!h) return DRSF_ENOMEM;
+    h->n = n;
+    h->flags = flags;
+    h->alloc = g_alloc;
+    h->dfree = g_free;
+    h->alloc_ctx = g_alloc_ctx;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return DRSF_ECUDA;
+    }
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+    if (nsm < 1 || !coop) {
+        delete h;
+        return DRSF_ECUDA;
+    }
+    h->dev.nsm = nsm;
+    h->dev.grid = (unsigned)nsm * 8u;
+    h->dev.coop_jump = coop_blocks_jump(nsm);
+    h->dev.coop_hook = coop_blocks_hook(nsm);
+    h->dev.coop_orient = coop_blocks_orient(nsm);
+    h->dev.coop_mark = coop_blocks_mark(nsm);
+    drsf_status st = create_impl(h, edges, m, parent, s);
+    if (st != DRSF_OK) {
+        destroy_all(h);
+        return st;
+    }
+    *out = h;
+    return DRSF_OK;
+}
+
+static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t len, cudaStream_t s) {
+    drsf_status st = ensure_batch(h, len, s);
+    if (st) return st;
+    st = storage_check(h, op, len, s);
+    if (st) return st;
+    Ctl *ctl = h->ctl;
+    Csr g{h->off, h->used, h->col};
+    CK(launch_begin(ctl, op, len, s));
+    CK(launch_validate_batch(batch, len, h->n, ctl, s));
+    if (op == DRSF_INSERT) {
+        // Algorithm 1, insert: F^ = F, M = B; rep of the previous batch is current
+        CK(launch_ins_claim(batch, len, h->ix, ctl, h->nkey, h->nslot, s));
+        CK(launch_ins_place(h->dev, h->nkey, h->nslot, ctl, g, h->ix, h->ovf, h->ovf_cap, h->rep, h->ck[0],
+                            h->ca[0], h->cb[0], h->cand_cap, s));
+    } else {
+        // Algorithm 1, delete: remove B, cut tree edges, re-label the cut trees
+        CK(launch_del_claim(batch, len, h->ix, g, h->ovf, h->parent, h->rep, ctl, h->aff_ep, h->cut_ep,
+                            h->cutlist, s));
+        CK(launch_aff_collect(h->dev, h->n, h->rep, h->aff_ep, h->parent, h->J0, h->A, ctl, s));
+        CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->J0, h->J1, h->rep, h->D, 1, s));
+        CK(launch_scan_rows(h->dev, h->D, ctl, g, h->rep, h->cut_ep, h->ck[0], h->ca[0], h->cb[0], h->cand_cap,
+                            s));
+        CK(launch_scan_ovf(h->dev, h->ovf, ctl, h->rep, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
+    }
+    CK(launch_boruvka(h->dev, ctl, h->ck[0], h->ca[0], h->cb[0], h->ck[1], h->ca[1], h->cb[1], h->comp, h->best0,
+                      h->best1, h->er, h->n, s));
+    OrientArgs oa{};
+    oa.er = h->er;
+    oa.rep = h->rep;
+    oa.comp = h->comp;
+    oa.minp = h->minp;
+    oa.pidx = h->pidx;
+    oa.plist = h->plist;
+    oa.pstamp = h->pstamp;
+    oa.pdeg = h->pdeg;
+    oa.pcur = h->pcur;
+    oa.poff = h->poff;
+    oa.adj = h->adj;
+    oa.apos = h->apos;
+    oa.val0 = h->val0;
+    oa.val1 = h->val1;
+    oa.nx0 = h->nx0;
+    oa.nx1 = h->nx1;
+    oa.bsum = h->bsum;
+    oa.chx = h->chx;
+    oa.chy = h->chy;
+    oa.att_ep = h->att_ep;
+    oa.rep_ep = h->rep_ep;
+    oa.att_x = h->att_x;
+    oa.newrep = h->newrep;
+    CK(launch_orient(h->dev, ctl, oa, s));
+    if (op == DRSF_INSERT)
+        CK(launch_active(h->dev, nullptr, 0, h->n, ctl, h->rep, h->parent, h->att_ep, h->att_x, h->rep_ep,
+                         h->newrep, h->act, h->pold, h->J0, h->mark, s));
+    else
+        CK(launch_active(h->dev, h->A, 1, 0, ctl, h->rep, h->parent, h->att_ep, h->att_x, h->rep_ep, h->newrep,
+                         h->act, h->pold, h->J0, h->mark, s));
+    CK(launch_mark(h->dev, ctl, h->act, h->J0, h->J1, h->mark, h->parent, s));
+    CK(launch_reverse(h->dev, ctl, h->act, h->pold, h->mark, h->chx, h->chy, h->parent, s));
+    return DRSF_OK;
+}
+
+drsf_status drsf_apply(drsf_handle h, drsf_op op, const int32_t *batch, int64_t len, drsf_stream stream) {
+    if (!h || (op != DRSF_INSERT && op != DRSF_DELETE) || len < 0 || (len > 0 && !batch)) return DRSF_EINVAL;
+    if (h->poisoned) return DRSF_EPOISONED;
+    if (len > (int64_t)1 << 31) return DRSF_EINVAL;
+    set_dev(h);
+    return apply_impl(h, (int)op, batch, len, (cudaStream_t)stream);
+}
+
+drsf_status drsf_apply_host(drsf_handle h, drsf_op op, const int32_t *batch, int64_t len, drsf_stream stream) {
+    if (!h || (op != DRSF_INSERT && op != DRSF_DELETE) || len < 0 || (len > 0 && !batch)) return DRSF_EINVAL;
+    if (h->poisoned) return DRSF_EPOISONED;
+    if (len > (int64_t)1 << 31) return DRSF_EINVAL;
+    set_dev(h);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (len > h->stage_cap) {
+        CK(cudaStreamSynchronize(s));
+        if (h->stage_host) cudaFreeHost(h->stage_host);
+        h->stage_host = nullptr;
+        hfree(h, &h->stage_dev, s);
+        long long cap = std::max<long long>(len, 1 << 16);
+        CK(cudaMallocHost((void **)&h->stage_host, (size_t)cap * 2 * sizeof(int)));
+        CKA(halloc(h, &h->stage_dev, (size_t)cap * 2, s));
+        h->stage_cap = cap;
+        if (!h->stage_done) CK(cudaEventCreateWithFlags(&h->stage_done, cudaEventDisableTiming));
+        h->stage_pending = false;
+    }
+    if (h->stage_pending) CK(cudaEventSynchronize(h->stage_done));   // previous copy out of the staging buffer
+    if (len > 0) {
+        memcpy(h->stage_host, batch, (size_t)len * 2 * sizeof(int));
+        CK(cudaMemcpyAsync(h->stage_dev, h->stage_host, (size_t)len * 2 * sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(cudaEventRecord(h->stage_done, s));
+        h->stage_pending = true;
+    }
+    return apply_impl(h, (int)op, h->stage_dev, len, s);
+}
+
+static drsf_status latched(drsf_ctx *h) {
+    int e = h->ctl_host->err;
+    if (e & (ERR_TIMEOUT | ERR_CAPACITY | ERR_ROUNDS)) {
+        h->poisoned = true;
+        return (e & ERR_TIMEOUT) ? DRSF_ETIMEOUT : DRSF_EPOISONED;
+    }
+    if (e & ERR_BATCH_ID) {
+        // report once, then clear the bit
+        int z = e & ~ERR_BATCH_ID;
+        cudaMemcpy(&h->ctl->err, &z, sizeof(int), cudaMemcpyHostToDevice);
+        return DRSF_EINVAL;
+    }
+    return DRSF_OK;
+}
+
+drsf_status drsf_sync(drsf_handle h, drsf_stream stream) {
+    if (!h) return DRSF_EINVAL;
+    if (h->poisoned) return DRSF_EPOISONED;
+    set_dev(h);
+    drsf_status st = read_ctl(h, (cudaStream_t)stream);
+    if (st) return st;
+    return latched(h);
+}
+
+drsf_status drsf_parent(drsf_handle h, int32_t *out, drsf_stream stream) {
+    if (!h || !out) return DRSF_EINVAL;
+    if (h->poisoned) return DRSF_EPOISONED;
+    set_dev(h);
+    CK(cudaMemcpyAsync(out, h->parent, (size_t)h->n * sizeof(int), cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream));
+    return DRSF_OK;
+}
+
+drsf_status drsf_labels(drsf_handle h, int32_t *out, drsf_stream stream) {
+    if (!h || !out) return DRSF_EINVAL;
+    if (h->poisoned) return DRSF_EPOISONED;
+    set_dev(h);
+    CK(launch_labels(h->n, h->rep, h->J1, out, (cudaStream_t)stream));
+    return DRSF_OK;
+}
+
+drsf_status drsf_stats(drsf_handle h, drsf_batch_stats *out, drsf_stream stream) {
+    if (!h || !out) return DRSF_EINVAL;
+    if (h->poisoned) return DRSF_EPOISONED;
+    set_dev(h);
+    drsf_status st = read_ctl(h, (cudaStream_t)stream);
+    if (st) return st;
+    const Ctl &c = *h->ctl_host;
+    out->batch_len = c.batch_len;
+    out->self_loops = c.self_loops;
+    out->dropped = c.dropped;
+    out->applied = (int64_t)c.nb;
+    out->tree_cut = (int64_t)c.ncut;
+    out->affected = (int64_t)c.naff;
+    out->detached = (int64_t)c.ndet;
+    out->scanned = c.scanned;
+    out->candidates = (int64_t)c.ncand;
+    out->hook_rounds = c.hook_rounds;
+    out->replacement = (int64_t)c.ner;
+    out->rank_rounds = c.rank_rounds;
+    out->active = (int64_t)c.nact;
+    out->reversed = c.reversed;
+    out->mark_rounds = c.mark_rounds;
+    out->jump_rounds = c.jump_rounds;
+    out->edges = c.edges;
+    out->overflow = (int64_t)c.ovf_count;
+    out->rebuilds = h->rebuilds;
+    return latched(h);
+}
+
+int32_t drsf_num_vertices(drsf_handle h) { return h ? h->n : 0; }
+
+int64_t drsf_num_edges(drsf_handle h, drsf_stream stream) {
+    drsf_batch_stats st;
+    if (drsf_stats(h, &st, stream) != DRSF_OK) return -1;
+    return st.edges;
+}
+
+drsf_status drsf_export_edges(drsf_handle h, int32_t *out, int64_t cap, int64_t *m_out, drsf_stream stream) {
+    if (!h || !m_out || cap < 0 || (cap > 0 && !out)) return DRSF_EINVAL;
+    if (h->poisoned) return DRSF_EPOISONED;
+    set_dev(h);
+    cudaStream_t s = (cudaStream_t)stream;
+    u64 *cnt = nullptr;
+    CKA(halloc(h, &cnt, 2, s));
+    CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(u64), s));
+    Csr g{h->off, h->used, h->col};
+    CK(launch_extract(h->dev, h->n, g, h->ovf, h->ovf_cap, h->ctl, out, cap, cnt, s));
+    u64 hc[2];
+    CK(cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    hfree(h, &cnt, s);
+    *m_out = (int64_t)hc[0];
+    return ((int *)hc)[2] ? DRSF_EINVAL : DRSF_OK;
+}
+
+void drsf_destroy(drsf_handle h) { destroy_all(h); }
+
+const char *drsf_error_string(drsf_status s) {
+    switch (s) {
+    case DRSF_OK: return "ok";
+    case DRSF_EINVAL: return "invalid argument or vertex id out of range";
+    case DRSF_ENOMEM: return "device memory allocation failed";
+    case DRSF_ECUDA: return "CUDA runtime error";
+    case DRSF_ENOT_FOREST: return "parent is not a rooted spanning forest of the graph";
+    case DRSF_ETIMEOUT: return "a bounded device-side wait timed out";
+    case DRSF_EPOISONED: return "handle unusable after an earlier device fault";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

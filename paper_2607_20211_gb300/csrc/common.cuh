@@ -1,0 +1,189 @@
+// Internal declarations shared by the kernels of the D-RSF library.
+//
+// Device state layout (all in HBM, one copy per handle):
+//   parent[n], rep[n]           int32   the forest and each vertex's tree root
+//   off[n+1]                    int64   slack-CSR row starts (row capacity =
+//                                       off[u+1] - off[u])
+//   used[n]                     int32   append cursor of each row
+//   col[off[n]]                 int32   neighbours; -1 = empty or deleted
+//   hkey[H], hpu[H], hpv[H]             open-addressing edge index: key ->
+//                                       global col positions of the edge in
+//                                       the rows of min(u,v) and max(u,v),
+//                                       or (POS_OVF, overflow slot)
+//   ovf[ovf_cap]                uint64  edges whose row had no free slot
+//   per-batch work arrays (epoch-stamped, never cleared per batch)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/drsf.h"
+
+typedef unsigned long long u64;
+
+#define EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
+#define TOMB_KEY 0xFFFFFFFFFFFFFFFEull
+#define POS_OVF 0xFFFFFFFFu
+#define NIL (-1)
+
+// latched device error bits (ctl->err)
+#define ERR_BATCH_ID 1   // out-of-range id in the current batch: batch skipped
+#define ERR_TIMEOUT 2    // a bounded grid barrier gave up
+#define ERR_CAPACITY 4   // an internal buffer would overflow (never expected)
+#define ERR_ROUNDS 8     // an iteration exceeded its round bound (cyclic parent)
+
+// grid-barrier wait limit in nanoseconds (globaltimer)
+#define BARRIER_TIMEOUT_NS 2000000000ull
+#define MAX_ROUNDS 40
+
+// Device control block: latched errors, batch epoch, grid barrier state,
+// per-batch counts.  Statistic fields mirror drsf_batch_stats.
+struct Ctl {
+    int err;
+    int skip;               // current batch rejected (ERR_BATCH_ID seen)
+    unsigned epoch;         // batch counter; epoch stamps compare against it
+    int op;
+    unsigned bar_count;
+    unsigned bar_gen;
+    int flag[3];            // per-round "another round needed" flags
+    u64 cnt[3];             // per-round list sizes (hook-and-compress)
+    u64 nb;                 // normalised batch edges (new / deleted keys)
+    u64 ncut;               // cut vertices
+    u64 naff;               // affected list
+    u64 ndet;               // detached list
+    u64 ncand;              // candidates
+    u64 ner;                // replacement edges
+    u64 npc;                // distinct pieces touched by E_r
+    u64 nact;               // active vertices (path reversal)
+    u64 ovf_count;          // overflow list length (grows until rebuild)
+    long long edges;        // live undirected edges of G
+    long long htomb;        // index tombstones
+    long long ctomb;        // CSR tombstones (deleted entries)
+    long long scanned;      // adjacency entries scanned
+    long long self_loops;
+    long long dropped;
+    long long tree_cut;
+    long long hook_rounds;
+    long long rank_rounds;
+    long long mark_rounds;
+    long long jump_rounds;
+    long long reversed;
+    long long batch_len;
+    long long overflow_total;
+};
+
+// The edge index.
+struct Index {
+    u64 *key;
+    uint32_t *pu;   // position of the edge in the row of min(u,v), or POS_OVF
+    uint32_t *pv;   // position in the row of max(u,v), or overflow slot
+    u64 mask;
+};
+
+// The slack CSR.
+struct Csr {
+    const long long *off;
+    int *used;
+    int *col;
+};
+
+__host__ __device__ __forceinline__ u64 ekey(uint32_t u, uint32_t v) {
+    return u < v ? ((u64)u << 32) | v : ((u64)v << 32) | u;
+}
+__host__ __device__ __forceinline__ uint32_t klo(u64 k) { return (uint32_t)(k >> 32); }
+__host__ __device__ __forceinline__ uint32_t khi(u64 k) { return (uint32_t)(k & 0xFFFFFFFFu); }
+
+// 64-bit finaliser (MurmurHash3 fmix64) for the edge index.
+__device__ __forceinline__ u64 hslot(u64 k, u64 mask) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k & mask;
+}
+
+// Warp-aggregated append: one atomicAdd per warp; returns the slot of this
+// lane (or -1 when pred is false).
+__device__ __forceinline__ long long agg_append(u64 *ctr, bool pred) {
+    unsigned active = __activemask();
+    unsigned m = __ballot_sync(active, pred);
+    if (!pred) return -1;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    u64 base = 0;
+    if (lane == leader) base = atomicAdd(ctr, (u64)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    return (long long)(base + __popc(m & ((1u << lane) - 1u)));
+}
+
+__device__ __forceinline__ u64 globaltimer_ns() {
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for cooperative launches (all blocks co-resident).
+// Generation-counting barrier; the wait is bounded: after
+// BARRIER_TIMEOUT_NS it latches ERR_TIMEOUT and every block returns false
+// from then on, so the kernel unwinds instead of hanging.
+__device__ __forceinline__ bool grid_barrier(Ctl *ctl) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &ctl->bar_gen;
+        volatile int *verr = &ctl->err;
+        unsigned g = *vgen;
+        __threadfence();
+        unsigned prev = atomicAdd(&ctl->bar_count, 1u);
+        int ok = 1;
+        if (prev == gridDim.x - 1) {
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            u64 t0 = globaltimer_ns();
+            while (*vgen == g) {
+                if (*verr & ERR_TIMEOUT) { ok = 0; break; }
+                if (globaltimer_ns() - t0 > BARRIER_TIMEOUT_NS) {
+                    atomicOr(&ctl->err, ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = ok && !(*verr & ERR_TIMEOUT);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Root search with path halving on a hook forest that is not being hooked
+// concurrently (halving writes keep every pointer on the path to the same
+// root).  The walk is bounded: a cycle (impossible for valid input) latches
+// ERR_ROUNDS instead of spinning.
+__device__ __forceinline__ int find_root(int *comp, int x, Ctl *ctl) {
+    for (int it = 0; it < (1 << 24); ++it) {
+        int p = __ldcg(&comp[x]);
+        if (p == x) return x;
+        int gp = __ldcg(&comp[p]);
+        if (gp == p) return p;
+        comp[x] = gp;
+        x = gp;
+    }
+    atomicOr(&ctl->err, ERR_ROUNDS);
+    return x;
+}
+
+// Loads of data that other blocks wrote earlier in the same cooperative
+// launch go to L2 (the SM's L1 may hold a stale line).
+#define LD(x) __ldcg(&(x))
+
+static inline unsigned grid_for(long long n, int block, unsigned cap) {
+    long long g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > (long long)cap) g = cap;
+    return (unsigned)g;
+}

@@ -1,0 +1,547 @@
+// Forest kernels of the D-RSF batch update (Algorithm 1):
+//   - representatives by pointer jumping on the cut forest F^;
+//   - replacement edges by hooking and compressing over the trees of F^
+//     (Section III-B, Algorithm 2, phase 1), with minimum-key hooking so
+//     that the chosen edges are the unique minimum spanning forest of the
+//     tree multigraph (Boruvka);
+//   - orientation of the replacement edges by an Euler tour of the
+//     tree-of-trees (Algorithm 2, phase 2; Euler tour technique, Section I
+//     preliminaries) rooted at the tree with the smallest root id;
+//   - path reversal of every (x, rep[x]) path at once by pointer doubling
+//     over the re-rooted trees, then attachment parent[x] <- y
+//     (Algorithm 1; ReversePaths, Section II-C), and the representative
+//     refresh.
+// Iterative phases run as one cooperative launch each with a bounded grid
+// barrier between rounds; no host round trip per round.
+#include <climits>
+
+#include "kernels.h"
+
+#define GS_LOOP(i, n) \
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)(n); \
+         i += (long long)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ long long gstride() { return (long long)gridDim.x * blockDim.x; }
+
+// Reset the per-batch counters and advance the epoch.
+__global__ void k_begin(Ctl *ctl, int op, long long len) {
+    if (threadIdx.x != 0) return;
+    ctl->epoch += 1;
+    ctl->skip = 0;
+    ctl->op = op;
+    ctl->nb = ctl->ncut = ctl->naff = ctl->ndet = ctl->ncand = ctl->ner = ctl->npc = ctl->nact = 0;
+    ctl->scanned = ctl->self_loops = ctl->dropped = ctl->tree_cut = 0;
+    ctl->hook_rounds = ctl->rank_rounds = ctl->mark_rounds = ctl->jump_rounds = ctl->reversed = 0;
+    ctl->batch_len = len;
+    for (int i = 0; i < 3; ++i) {
+        ctl->flag[i] = 0;
+        ctl->cnt[i] = 0;
+    }
+}
+
+// Delete: list the vertices of every tree that lost a tree edge (its old
+// root was stamped by the cut) and seed J0 = parent (the cut forest F^).
+__global__ void k_aff_collect(int n, const int *rep, const unsigned *aff_ep, const int *parent, int *J0, int *A,
+                              Ctl *ctl) {
+    if (*(volatile int *)&ctl->skip) return;
+    unsigned ep = ctl->epoch;
+    GS_LOOP(v, n) {
+        bool in = aff_ep[rep[v]] == ep;
+        long long p = agg_append(&ctl->naff, in);
+        if (in) {
+            A[p] = (int)v;
+            J0[v] = parent[v];
+        }
+    }
+}
+
+__global__ void k_copy(int n, const int *src, int *dst) {
+    GS_LOOP(v, n) dst[v] = src[v];
+}
+
+// Representatives (Algorithm 1, parallel pointer jumping): J <- J o J over
+// the listed vertices until no pointer moves; then rep[v] = J[v].  Ping-pong
+// buffers keep every round a pure function of the previous one.  In delete
+// mode (1) a vertex whose new root differs from its old rep is detached and
+// listed in D.
+__global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J0, int *J1, int *rep,
+                       int *D, int mode) {
+    if (*(volatile int *)&ctl->skip) return;
+    long long cnt = use_list ? (long long)ctl->naff : cnt_static;
+    int *Jc = J0, *Jn = J1;
+    int r = 0;
+    for (;; ++r) {
+        if (r >= MAX_ROUNDS) {
+            if (gtid() == 0) atomicOr(&ctl->err, ERR_ROUNDS);
+            return;
+        }
+        if (gtid() == 0) ctl->flag[(r + 1) % 3] = 0;
+        bool ch = false;
+        for (long long i = gtid(); i < cnt; i += gstride()) {
+            int v = use_list ? A[i] : (int)i;
+            int w = LD(Jc[v]);
+            int w2 = LD(Jc[w]);
+            Jn[v] = w2;
+            ch |= (w2 != w);
+        }
+        if (__syncthreads_or(ch) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
+        if (!grid_barrier(ctl)) return;
+        int again = *(volatile int *)&ctl->flag[r % 3];
+        int *t = Jc; Jc = Jn; Jn = t;
+        if (!again) break;
+    }
+    for (long long i = gtid(); i < cnt; i += gstride()) {
+        int v = use_list ? A[i] : (int)i;
+        int root = LD(Jc[v]);
+        bool det = mode == 1 && root != rep[v];
+        rep[v] = root;
+        long long p = agg_append(&ctl->ndet, det);
+        if (det) D[p] = v;
+    }
+    if (gtid() == 0) ctl->jump_rounds = r + 1;
+}
+
+// Replacement edges by hook-and-compress over the trees of F^ (pieces).
+// Each round: every component takes the minimum key among its incident
+// candidates (64-bit atomicMin); a component whose minimum edge leads to
+// another component hooks onto it (a mutual choice hooks the larger id under
+// the smaller); each hooking edge joins E_r.  Candidates inside one
+// component are dropped, the rest are compacted for the next round.  With
+// distinct keys this is Boruvka's algorithm: E_r is the unique minimum
+// spanning forest of the piece multigraph, |E_r| = k - l.
+__global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1, int *comp,
+                          u64 *best0, u64 *best1, u64 *er, long long er_cap) {
+    if (*(volatile int *)&ctl->skip) return;
+    long long c0 = (long long)ctl->ncand;
+    for (long long i = gtid(); i < c0; i += gstride()) {
+        int a = ca0[i], b = cb0[i];
+        comp[a] = a;
+        comp[b] = b;
+        best0[a] = best0[b] = EMPTY_KEY;
+        best1[a] = best1[b] = EMPTY_KEY;
+    }
+    if (gtid() == 0) {
+        ctl->cnt[0] = (u64)c0;
+        ctl->cnt[1] = ctl->cnt[2] = 0;
+        ctl->flag[0] = ctl->flag[1] = ctl->flag[2] = 0;
+    }
+    if (!grid_barrier(ctl)) return;
+    int r = 0;
+    for (;; ++r) {
+        if (r >= MAX_ROUNDS) {
+            if (gtid() == 0) atomicOr(&ctl->err, ERR_ROUNDS);
+            return;
+        }
+        u64 *ck = (r & 1) ? ck1 : ck0, *ckn = (r & 1) ? ck0 : ck1;
+        int *ca = (r & 1) ? ca1 : ca0, *can = (r & 1) ? ca0 : ca1;
+        int *cb = (r & 1) ? cb1 : cb0, *cbn = (r & 1) ? cb0 : cb1;
+        u64 *best = (r & 1) ? best1 : best0, *bestn = (r & 1) ? best0 : best1;
+        long long c = (long long)*(volatile u64 *)&ctl->cnt[r % 3];
+        if (gtid() == 0) {
+            ctl->cnt[(r + 2) % 3] = 0;
+            ctl->flag[(r + 1) % 3] = 0;
+        }
+        // phase A: roots of both ends, per-component minimum key
+        for (long long i = gtid(); i < c; i += gstride()) {
+            int a = find_root(comp, LD(ca[i]), ctl), b = find_root(comp, LD(cb[i]), ctl);
+            ca[i] = a;
+            cb[i] = b;
+            if (a != b) {
+                u64 k = LD(ck[i]);
+                atomicMin(&best[a], k);
+                atomicMin(&best[b], k);
+            }
+        }
+        if (!grid_barrier(ctl)) return;
+        // phase B: hook along minimum edges, keep the rest
+        bool hooked = false;
+        for (long long i = gtid(); i < c; i += gstride()) {
+            int a = LD(ca[i]), b = LD(cb[i]);
+            bool alive = a != b;
+            bool hook = false, keep = false;
+            u64 k = LD(ck[i]);
+            if (alive) {
+                bool ba = __ldcg(&best[a]) == k, bb = __ldcg(&best[b]) == k;
+                if (ba && bb) comp[a > b ? a : b] = a > b ? b : a;
+                else if (ba) comp[a] = b;
+                else if (bb) comp[b] = a;
+                hook = ba || bb;
+                keep = !hook;
+                bestn[a] = EMPTY_KEY;
+                bestn[b] = EMPTY_KEY;
+            }
+            hooked |= hook;
+            long long pe = agg_append(&ctl->ner, hook);
+            if (hook) {
+                if (pe < er_cap) er[pe] = k;
+                else atomicOr(&ctl->err, ERR_CAPACITY);
+            }
+            long long pk = agg_append(&ctl->cnt[(r + 1) % 3], keep);
+            if (keep) {
+                ckn[pk] = k;
+                can[pk] = a;
+                cbn[pk] = b;
+            }
+        }
+        if (__syncthreads_or(hooked) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
+        if (!grid_barrier(ctl)) return;
+        if (!*(volatile int *)&ctl->flag[r % 3]) break;
+    }
+    if (gtid() == 0) ctl->hook_rounds = r;
+}
+
+// Block-wide exclusive scan of int (BLK threads); *total receives the sum.
+__device__ int block_excl_scan(int v, int *total) {
+    __shared__ int ws[BLK / 32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < BLK / 32 ? ws[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < BLK / 32) ws[lane] = t;
+    }
+    __syncthreads();
+    int pre = (w > 0 ? ws[w - 1] : 0) + x - v;
+    *total = ws[BLK / 32 - 1];
+    __syncthreads();
+    return pre;
+}
+
+// Orientation of E_r (Algorithm 2, phase 2).  The replacement edges form a
+// forest over the pieces (the super-forest).  Each super-tree is rooted at
+// its piece with the smallest root id: build the Euler circuit of each
+// super-tree from the circular adjacency lists (successor of arc a->b is the
+// arc after b->a in b's list), open it at the root, rank the arcs by
+// Wyllie's pointer jumping, and orient each edge from the arc that comes
+// first.  The child piece P of edge {x, y} (x in P) gets the oriented
+// replacement edge x -> y; every piece of the super-tree gets the new root.
+__global__ void k_orient(Ctl *ctl, OrientArgs a) {
+    if (*(volatile int *)&ctl->skip) return;
+    const long long ner = (long long)ctl->ner;
+    const unsigned ep = ctl->epoch;
+    // phase 1: dense ids for the pieces touched by E_r, minp init
+    for (long long i = gtid(); i < 2 * ner; i += gstride()) {
+        u64 k = a.er[i >> 1];
+        int p = a.rep[(i & 1) ? khi(k) : klo(k)];
+        int root = find_root(a.comp, p, ctl);
+        a.minp[root] = INT_MAX;
+        if (atomicExch(&a.pstamp[p], ep) != ep) {
+            long long id = (long long)atomicAdd(&ctl->npc, 1ull);
+            a.pidx[p] = (int)id;
+            a.plist[id] = p;
+            a.pdeg[id] = 0;
+            a.pcur[id] = 0;
+        }
+    }
+    if (!grid_barrier(ctl)) return;
+    // phase 2: smallest piece id per super-tree, degrees
+    for (long long i = gtid(); i < 2 * ner; i += gstride()) {
+        u64 k = a.er[i >> 1];
+        int p = a.rep[(i & 1) ? khi(k) : klo(k)];
+        atomicMin(&a.minp[find_root(a.comp, p, ctl)], p);
+        atomicAdd(&a.pdeg[LD(a.pidx[p])], 1);
+    }
+    if (!grid_barrier(ctl)) return;
+    // phase 3: exclusive scan of degrees -> adjacency offsets
+    const long long np = (long long)*(volatile u64 *)&ctl->npc;
+    const long long chunk = (np + gridDim.x - 1) / gridDim.x;
+    const long long lo = (long long)blockIdx.x * chunk, hi = lo + chunk < np ? lo + chunk : np;
+    {
+        int s = 0;
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) s += LD(a.pdeg[i]);
+        int tot;
+        block_excl_scan(s, &tot);
+        if (threadIdx.x == 0) a.bsum[blockIdx.x] = tot;
+    }
+    if (!grid_barrier(ctl)) return;
+    if (blockIdx.x == 0) {
+        long long nbk = gridDim.x;
+        long long per = (nbk + BLK - 1) / BLK;
+        long long l0 = threadIdx.x * per, l1 = l0 + per < nbk ? l0 + per : nbk;
+        int s = 0;
+        for (long long i = l0; i < l1; ++i) s += (int)LD(a.bsum[i]);
+        int tot;
+        int pre = block_excl_scan(s, &tot);
+        for (long long i = l0; i < l1; ++i) {
+            long long t = LD(a.bsum[i]);
+            a.bsum[i] = pre;
+            pre += (int)t;
+        }
+    }
+    if (!grid_barrier(ctl)) return;
+    {
+        int carry = (int)LD(a.bsum[blockIdx.x]);
+        for (long long t0 = lo; t0 < hi; t0 += blockDim.x) {
+            long long i = t0 + threadIdx.x;
+            int d = i < hi ? LD(a.pdeg[i]) : 0;
+            int tot;
+            int pre = block_excl_scan(d, &tot);
+            if (i < hi) a.poff[i] = carry + pre;
+            carry += tot;
+        }
+    }
+    if (!grid_barrier(ctl)) return;
+    // phase 4: place arcs; arc 2i = (lo-piece -> hi-piece), arc 2i+1 its twin
+    for (long long i = gtid(); i < 2 * ner; i += gstride()) {
+        u64 k = a.er[i >> 1];
+        int p = a.rep[(i & 1) ? khi(k) : klo(k)];
+        int id = LD(a.pidx[p]);
+        int slot = LD(a.poff[id]) + atomicAdd(&a.pcur[id], 1);
+        a.adj[slot] = (int)i;
+        a.apos[i] = slot;
+    }
+    if (!grid_barrier(ctl)) return;
+    // phase 5: Euler successors; open the circuit at each super-root
+    for (long long i = gtid(); i < 2 * ner; i += gstride()) {
+        long long tw = i ^ 1;
+        u64 k = a.er[i >> 1];
+        int head = a.rep[(i & 1) ? klo(k) : khi(k)];     // source of the twin
+        int id = LD(a.pidx[head]);
+        int start = LD(a.poff[id]), end = start + LD(a.pdeg[id]);
+        int nx = LD(a.apos[tw]) + 1;
+        int succ;
+        if (nx == end) {
+            bool is_root = LD(a.minp[find_root(a.comp, head, ctl)]) == head;
+            succ = is_root ? NIL : LD(a.adj[start]);
+        } else {
+            succ = LD(a.adj[nx]);
+        }
+        a.nx0[i] = succ;
+        a.val0[i] = 1;
+    }
+    if (!grid_barrier(ctl)) return;
+    // phase 6: list ranking (Wyllie): val = arcs from here to the tour end
+    int *vc = a.val0, *vn = a.val1, *nc = a.nx0, *nn = a.nx1;
+    int r = 0;
+    for (;; ++r) {
+        if (r >= MAX_ROUNDS) {
+            if (gtid() == 0) atomicOr(&ctl->err, ERR_ROUNDS);
+            return;
+        }
+        if (gtid() == 0) ctl->flag[(r + 1) % 3] = 0;
+        bool ch = false;
+        for (long long i = gtid(); i < 2 * ner; i += gstride()) {
+            int s = LD(nc[i]);
+            if (s != NIL) {
+                vn[i] = LD(vc[i]) + LD(vc[s]);
+                nn[i] = LD(nc[s]);
+                ch = true;
+            } else {
+                vn[i] = LD(vc[i]);
+                nn[i] = NIL;
+            }
+        }
+        if (__syncthreads_or(ch) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
+        if (!grid_barrier(ctl)) return;
+        int again = *(volatile int *)&ctl->flag[r % 3];
+        int *t = vc; vc = vn; vn = t;
+        t = nc; nc = nn; nn = t;
+        if (!again) break;
+    }
+    // phase 7: orient, attach points, new roots
+    for (long long i = gtid(); i < ner; i += gstride()) {
+        u64 k = a.er[i];
+        int x0 = (int)klo(k), x1 = (int)khi(k);
+        int p0 = a.rep[x0], p1 = a.rep[x1];
+        bool down = LD(vc[2 * i]) > LD(vc[2 * i + 1]);   // arc p0 -> p1 first: p0 is the parent
+        int child = down ? p1 : p0;
+        int x = down ? x1 : x0, y = down ? x0 : x1;
+        a.chx[i] = x;
+        a.chy[i] = y;
+        a.att_x[child] = x;
+        a.att_ep[child] = ep;
+        int nr0 = LD(a.minp[find_root(a.comp, p0, ctl)]);
+        a.newrep[p0] = nr0;
+        a.newrep[p1] = nr0;
+        a.rep_ep[p0] = ep;
+        a.rep_ep[p1] = ep;
+    }
+    if (gtid() == 0) ctl->rank_rounds = r + 1;
+}
+
+// Path-reversal set-up fused with the representative refresh: a vertex of a
+// piece that is re-rooted at an attach point x != its root is active (its
+// old parent is saved, J0 seeded, x marked); every vertex of a merged piece
+// takes the super-tree's root as its new rep.
+__global__ void k_active(const int *L, int use_list, long long cnt_static, Ctl *ctl, int *rep, const int *parent,
+                         const unsigned *att_ep, const int *att_x, const unsigned *rep_ep, const int *newrep,
+                         int *act, int *pold, int *J0, unsigned char *mark) {
+    if (*(volatile int *)&ctl->skip) return;
+    unsigned ep = ctl->epoch;
+    long long cnt = use_list ? (long long)ctl->naff : cnt_static;
+    GS_LOOP(i, cnt) {
+        int v = use_list ? L[i] : (int)i;
+        int p = rep[v];
+        bool on = false;
+        int x = -1;
+        if (att_ep[p] == ep) {
+            x = att_x[p];
+            on = x != p;
+        }
+        long long q = agg_append(&ctl->nact, on);
+        if (on) {
+            int pv = parent[v];
+            act[q] = v;
+            pold[q] = pv;
+            J0[v] = pv;
+            mark[v] = v == x;
+        }
+        if (rep_ep[p] == ep) rep[v] = newrep[p];
+    }
+}
+
+// Mark every ancestor of each attach point x inside its piece by pointer
+// doubling over the active vertices: round j, a marked v marks J_j[v] (its
+// 2^j-th ancestor, clamped at the root) and J_{j+1} = J_j o J_j.  After
+// round j the marks cover distances [0, 2^{j+1}); the loop stops once every
+// J_{j+1} is a root, which bounds the path length.  Marks only ever land on
+// ancestors of x, so reads racing with writes within a round are harmless.
+__global__ void k_mark(Ctl *ctl, const int *act, int *J0, int *J1, unsigned char *mark, const int *parent) {
+    if (*(volatile int *)&ctl->skip) return;
+    long long na = (long long)ctl->nact;
+    int *Jc = J0, *Jn = J1;
+    int r = 0;
+    for (;; ++r) {
+        if (r >= MAX_ROUNDS) {
+            if (gtid() == 0) atomicOr(&ctl->err, ERR_ROUNDS);
+            return;
+        }
+        if (gtid() == 0) ctl->flag[(r + 1) % 3] = 0;
+        bool more = false;
+        for (long long i = gtid(); i < na; i += gstride()) {
+            int v = act[i];
+            int w = LD(Jc[v]);
+            if (LD(mark[v])) mark[w] = 1;
+            int w2 = LD(Jc[w]);
+            Jn[v] = w2;
+            more |= parent[w2] != w2;
+        }
+        if (__syncthreads_or(more) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
+        if (!grid_barrier(ctl)) return;
+        int again = *(volatile int *)&ctl->flag[r % 3];
+        int *t = Jc; Jc = Jn; Jn = t;
+        if (!again) break;
+    }
+    if (gtid() == 0) ctl->mark_rounds = r + 1;
+}
+
+// ReversePaths + attach (Algorithm 1): for each marked non-root vertex u,
+// parent'[old parent of u] = u (old parents come from the saved snapshot, so
+// no thread reads a pointer another thread rewrites); then parent[x] = y for
+// every oriented replacement edge x -> y.
+__global__ void k_reverse(Ctl *ctl, const int *act, const int *pold, const unsigned char *mark, const int *chx,
+                          const int *chy, int *parent) {
+    if (*(volatile int *)&ctl->skip) return;
+    long long na = (long long)ctl->nact, ner = (long long)ctl->ner;
+    GS_LOOP(i, na) {
+        int v = act[i];
+        int p = pold[i];
+        if (mark[v] && p != v) parent[p] = v;
+    }
+    GS_LOOP(i, ner) parent[chx[i]] = chy[i];
+}
+
+__global__ void k_count_reversed(Ctl *ctl, const int *act, const int *pold, const unsigned char *mark) {
+    if (*(volatile int *)&ctl->skip) return;
+    long long na = (long long)ctl->nact;
+    long long c = 0;
+    GS_LOOP(i, na) c += (mark[act[i]] && pold[i] != act[i]) ? 1 : 0;
+    if (c) atomicAdd((u64 *)&ctl->reversed, (u64)c);
+}
+
+// Component labels: smallest vertex id per tree (drsf_labels).
+__global__ void k_label_init(int n, int *tmp) {
+    GS_LOOP(v, n) tmp[v] = INT_MAX;
+}
+__global__ void k_label_min(int n, const int *rep, int *tmp) {
+    GS_LOOP(v, n) {
+        int r = rep[v];
+        unsigned same = __match_any_sync(__activemask(), r);
+        // lanes hold increasing v: the lowest lane of each group has the minimum
+        if ((threadIdx.x & 31) == __ffs(same) - 1) atomicMin(&tmp[r], (int)v);
+    }
+}
+__global__ void k_label_out(int n, const int *rep, const int *tmp, int *out) {
+    GS_LOOP(v, n) out[v] = tmp[rep[v]];
+}
+
+// ------------------------------------------------------------- wrappers
+
+static unsigned gsz(long long n) { return grid_for(n, BLK, 152u * 16u); }
+
+static unsigned coop_blocks(const void *fn, int nsm, int cap_per_sm) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, BLK, 0) != cudaSuccess || per < 1) per = 1;
+    if (per > cap_per_sm) per = cap_per_sm;
+    return (unsigned)(per * nsm);
+}
+unsigned coop_blocks_jump(int nsm) { return coop_blocks((const void *)k_jump, nsm, 4); }
+unsigned coop_blocks_hook(int nsm) { return coop_blocks((const void *)k_boruvka, nsm, 4); }
+unsigned coop_blocks_orient(int nsm) { return coop_blocks((const void *)k_orient, nsm, 2); }
+unsigned coop_blocks_mark(int nsm) { return coop_blocks((const void *)k_mark, nsm, 4); }
+
+cudaError_t launch_begin(Ctl *ctl, int op, long long len, cudaStream_t s) {
+    k_begin<<<1, 32, 0, s>>>(ctl, op, len);
+    return cudaGetLastError();
+}
+cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, const int *parent,
+                               int *J0, int *A, Ctl *ctl, cudaStream_t s) {
+    k_aff_collect<<<gsz(n), BLK, 0, s>>>(n, rep, aff_ep, parent, J0, A, ctl);
+    (void)d;
+    return cudaGetLastError();
+}
+cudaError_t launch_copy_parent(int n, const int *parent, int *J0, cudaStream_t s) {
+    k_copy<<<gsz(n), BLK, 0, s>>>(n, parent, J0);
+    return cudaGetLastError();
+}
+cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J0,
+                        int *J1, int *rep, int *D, int mode, cudaStream_t s) {
+    void *args[] = {(void *)&A, (void *)&use_list, (void *)&cnt_static, (void *)&ctl, (void *)&J0,
+                    (void *)&J1, (void *)&rep, (void *)&D, (void *)&mode};
+    return cudaLaunchCooperativeKernel((const void *)k_jump, d.coop_jump, BLK, args, 0, s);
+}
+cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
+                           int *comp, u64 *best0, u64 *best1, u64 *er, long long er_cap, cudaStream_t s) {
+    void *args[] = {(void *)&ctl, (void *)&ck0, (void *)&ca0, (void *)&cb0, (void *)&ck1, (void *)&ca1,
+                    (void *)&cb1, (void *)&comp, (void *)&best0, (void *)&best1, (void *)&er, (void *)&er_cap};
+    return cudaLaunchCooperativeKernel((const void *)k_boruvka, d.coop_hook, BLK, args, 0, s);
+}
+cudaError_t launch_orient(const Dev &d, Ctl *ctl, OrientArgs a, cudaStream_t s) {
+    void *args[] = {(void *)&ctl, (void *)&a};
+    return cudaLaunchCooperativeKernel((const void *)k_orient, d.coop_orient, BLK, args, 0, s);
+}
+cudaError_t launch_active(const Dev &d, const int *L, int use_list, long long cnt_static, Ctl *ctl, int *rep,
+                          const int *parent, const unsigned *att_ep, const int *att_x, const unsigned *rep_ep,
+                          const int *newrep, int *act, int *pold, int *J0, unsigned char *mark, cudaStream_t s) {
+    unsigned g = use_list ? d.grid : gsz(cnt_static);
+    k_active<<<g, BLK, 0, s>>>(L, use_list, cnt_static, ctl, rep, parent, att_ep, att_x, rep_ep, newrep, act,
+                                pold, J0, mark);
+    return cudaGetLastError();
+}
+cudaError_t launch_mark(const Dev &d, Ctl *ctl, const int *act, int *J0, int *J1, unsigned char *mark,
+                        const int *parent, cudaStream_t s) {
+    void *args[] = {(void *)&ctl, (void *)&act, (void *)&J0, (void *)&J1, (void *)&mark, (void *)&parent};
+    return cudaLaunchCooperativeKernel((const void *)k_mark, d.coop_mark, BLK, args, 0, s);
+}
+cudaError_t launch_reverse(const Dev &d, Ctl *ctl, const int *act, const int *pold, const unsigned char *mark,
+                           const int *chx, const int *chy, int *parent, cudaStream_t s) {
+    k_count_reversed<<<d.grid, BLK, 0, s>>>(ctl, act, pold, mark);
+    k_reverse<<<d.grid, BLK, 0, s>>>(ctl, act, pold, mark, chx, chy, parent);
+    return cudaGetLastError();
+}
+cudaError_t launch_labels(int n, const int *rep, int *tmp, int *out, cudaStream_t s) {
+    k_label_init<<<gsz(n), BLK, 0, s>>>(n, tmp);
+    k_label_min<<<gsz(n), BLK, 0, s>>>(n, rep, tmp);
+    k_label_out<<<gsz(n), BLK, 0, s>>>(n, rep, tmp, out);
+    return cudaGetLastError();
+}

@@ -1,0 +1,527 @@
+// Graph storage kernels: slack CSR + edge index build, batch normalisation,
+// insertion and deletion of the batch ("Insert/Delete B of edges to/from G",
+// Algorithm 1), and the cross-edge scans that produce the candidate set
+// (key edges with rep[u] != rep[v], Section II-A).
+#include <climits>
+
+#include "kernels.h"
+
+#define GS_LOOP(i, n) \
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)(n); \
+         i += (long long)gridDim.x * blockDim.x)
+
+// Warp-aggregated counter increment.
+__device__ __forceinline__ void agg_count(long long *ctr, bool pred, long long sign = 1) {
+    unsigned m = __ballot_sync(__activemask(), pred);
+    if (m && (threadIdx.x & 31) == __ffs(m) - 1 && pred)
+        atomicAdd((u64 *)ctr, (u64)(sign * (long long)__popc(m)));
+}
+
+// Insert-if-absent.  Returns the slot when this call claimed it, -1-slot
+// when the key was already present, LLONG_MIN when the table is full.
+__device__ long long index_claim(Index ix, u64 key) {
+    u64 s = hslot(key, ix.mask);
+    for (u64 p = 0; p <= ix.mask; ++p) {
+        u64 cur = __ldcg(&ix.key[s]);
+        if (cur == key) return -1 - (long long)s;
+        if (cur == EMPTY_KEY) {
+            u64 old = atomicCAS(&ix.key[s], EMPTY_KEY, key);
+            if (old == EMPTY_KEY) return (long long)s;
+            if (old == key) return -1 - (long long)s;
+        }
+        s = (s + 1) & ix.mask;
+    }
+    return LLONG_MIN;
+}
+
+// Lookup; -1 when absent.  Deleted entries (TOMB_KEY) are probed past.
+__device__ long long index_find(Index ix, u64 key) {
+    u64 s = hslot(key, ix.mask);
+    for (u64 p = 0; p <= ix.mask; ++p) {
+        u64 cur = __ldcg(&ix.key[s]);
+        if (cur == key) return (long long)s;
+        if (cur == EMPTY_KEY) return -1;
+        s = (s + 1) & ix.mask;
+    }
+    return -1;
+}
+
+// ------------------------------------------------------------------ build
+
+__global__ void k_check_range(const int *a, long long cnt, int n, int *bad) {
+    GS_LOOP(i, cnt) {
+        int x = a[i];
+        if (x < 0 || x >= n) atomicOr(bad, 1);
+    }
+}
+
+// Deduplicate the input edge list through the index; winners are appended.
+__global__ void k_create_claim(const int *edges, long long m, Index ix, u64 *dkey, u64 *dslot, u64 *cnt,
+                               long long *self_loops) {
+    GS_LOOP(i, m) {
+        int u = edges[2 * i], v = edges[2 * i + 1];
+        bool keep = false;
+        u64 key = 0;
+        long long s = -1;
+        if (u != v) {
+            key = ekey((uint32_t)u, (uint32_t)v);
+            s = index_claim(ix, key);
+            keep = s >= 0;
+        }
+        agg_count(self_loops, u == v);
+        long long p = agg_append(cnt, keep);
+        if (keep) {
+            dkey[p] = key;
+            dslot[p] = (u64)s;
+        }
+    }
+}
+
+__global__ void k_degree(const u64 *dkey, long long m, int *deg) {
+    GS_LOOP(i, m) {
+        u64 k = dkey[i];
+        atomicAdd(&deg[klo(k)], 1);
+        atomicAdd(&deg[khi(k)], 1);
+    }
+}
+
+// Row capacity: degree plus max(4, degree / 4) free slots.
+__global__ void k_caps(const int *deg, int n, long long *cap) {
+    GS_LOOP(u, n) {
+        int d = deg[u];
+        int slack = d / 4 > 4 ? d / 4 : 4;
+        cap[u] = (long long)d + slack;
+    }
+}
+
+// Exclusive scan of int64: tiles of SCAN_TILE elements.
+#define SCAN_ITEMS 16
+#define SCAN_TILE (BLK * SCAN_ITEMS)
+
+__device__ long long block_excl_scan_i64(long long v, long long *total) {
+    __shared__ long long ws[BLK / 32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        long long t = lane < BLK / 32 ? ws[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < BLK / 32) ws[lane] = t;
+    }
+    __syncthreads();
+    long long pre = (w > 0 ? ws[w - 1] : 0) + x - v;
+    *total = ws[BLK / 32 - 1];
+    __syncthreads();
+    return pre;
+}
+
+__global__ void k_scan_tiles(const long long *in, long long n, long long *bsum) {
+    long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
+    long long s = 0;
+    for (int j = 0; j < SCAN_ITEMS; ++j)
+        if (base + j < n) s += in[base + j];
+    long long tot;
+    block_excl_scan_i64(s, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(long long *bsum, long long nb) {
+    // one block: exclusive scan of nb block sums in place
+    long long per = (nb + BLK - 1) / BLK;
+    long long lo = threadIdx.x * per, hi = lo + per < nb ? lo + per : nb;
+    long long s = 0;
+    for (long long i = lo; i < hi; ++i) s += bsum[i];
+    long long tot;
+    long long pre = block_excl_scan_i64(s, &tot);
+    for (long long i = lo; i < hi; ++i) {
+        long long t = bsum[i];
+        bsum[i] = pre;
+        pre += t;
+    }
+}
+
+__global__ void k_scan_apply(const long long *in, long long *out, long long n, const long long *bsum) {
+    long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
+    long long s = 0;
+    for (int j = 0; j < SCAN_ITEMS; ++j)
+        if (base + j < n) s += in[base + j];
+    long long tot;
+    long long pre = block_excl_scan_i64(s, &tot) + bsum[blockIdx.x];
+    for (int j = 0; j < SCAN_ITEMS; ++j)
+        if (base + j < n) {
+            out[base + j] = pre;
+            pre += in[base + j];
+        }
+    if (base <= n - 1 && base + SCAN_ITEMS > n - 1) out[n] = pre;   // total after the last element
+}
+
+// Place the deduplicated edges: append to both rows, record positions.
+__global__ void k_fill(const u64 *dkey, const u64 *dslot, long long m, Csr g, Index ix) {
+    GS_LOOP(i, m) {
+        u64 k = dkey[i];
+        uint32_t a = klo(k), b = khi(k);
+        int pa = atomicAdd(&g.used[a], 1), pb = atomicAdd(&g.used[b], 1);
+        long long qa = g.off[a] + pa, qb = g.off[b] + pb;
+        g.col[qa] = (int)b;
+        g.col[qb] = (int)a;
+        ix.pu[dslot[i]] = (uint32_t)qa;
+        ix.pv[dslot[i]] = (uint32_t)qb;
+    }
+}
+
+// ------------------------------------------------------------ per batch
+
+__global__ void k_validate_batch(const int *batch, long long len, int n, Ctl *ctl) {
+    GS_LOOP(i, 2 * len) {
+        int x = batch[i];
+        if (x < 0 || x >= n) {
+            atomicOr(&ctl->err, ERR_BATCH_ID);
+            ctl->skip = 1;
+        }
+    }
+}
+
+// Insert, step 1 (batch normalisation): drop self-loops, repeated pairs and
+// edges already in G; claim an index slot for each new edge.
+__global__ void k_ins_claim(const int *batch, long long len, Index ix, Ctl *ctl, u64 *nkey, u64 *nslot) {
+    if (*(volatile int *)&ctl->skip) return;
+    GS_LOOP(i, len) {
+        int u = batch[2 * i], v = batch[2 * i + 1];
+        bool keep = false, drop = false;
+        u64 key = 0;
+        long long s = -1;
+        if (u != v) {
+            key = ekey((uint32_t)u, (uint32_t)v);
+            s = index_claim(ix, key);
+            if (s == LLONG_MIN) atomicOr(&ctl->err, ERR_CAPACITY);
+            keep = s >= 0;
+            drop = !keep;
+        }
+        agg_count(&ctl->self_loops, u == v);
+        agg_count(&ctl->dropped, drop);
+        long long p = agg_append(&ctl->nb, keep);
+        if (keep) {
+            nkey[p] = key;
+            nslot[p] = (u64)s;
+        }
+    }
+}
+
+// Insert, step 2: append each new edge to both CSR rows (warp-aggregated
+// row cursors are per row, so plain atomics); an edge whose row is full goes
+// whole to the overflow list.  The cross test of the insert case (M = B,
+// Algorithm 1) is fused here: rep[u] != rep[v] makes a candidate.
+__global__ void k_ins_place(const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, Index ix, u64 *ovf, u64 ovf_cap,
+                            const int *rep, u64 *ck, int *ca, int *cb, u64 cand_cap) {
+    if (*(volatile int *)&ctl->skip) return;
+    long long nb = (long long)ctl->nb;
+    GS_LOOP(i, nb) {
+        u64 k = nkey[i];
+        u64 s = nslot[i];
+        uint32_t a = klo(k), b = khi(k);
+        long long oa = g.off[a], ob = g.off[b];
+        long long capa = g.off[a + 1] - oa, capb = g.off[b + 1] - ob;
+        int pa = atomicAdd(&g.used[a], 1), pb = atomicAdd(&g.used[b], 1);
+        bool fa = pa < capa, fb = pb < capb;
+        if (fa && fb) {
+            g.col[oa + pa] = (int)b;
+            g.col[ob + pb] = (int)a;
+            ix.pu[s] = (uint32_t)(oa + pa);
+            ix.pv[s] = (uint32_t)(ob + pb);
+        } else {
+            // the consumed free slot (if any) stays -1
+            u64 o = atomicAdd(&ctl->ovf_count, 1ull);
+            if (o < ovf_cap) {
+                ovf[o] = k;
+                ix.pu[s] = POS_OVF;
+                ix.pv[s] = (uint32_t)o;
+            } else {
+                atomicOr(&ctl->err, ERR_CAPACITY);
+            }
+            atomicAdd((u64 *)&ctl->overflow_total, 1ull);
+            if (fa || fb) atomicAdd((u64 *)&ctl->ctomb, 1ull);
+        }
+        int ra = rep[a], rb = rep[b];
+        bool cross = ra != rb;
+        long long p = agg_append(&ctl->ncand, cross);
+        if (cross) {
+            if ((u64)p < cand_cap) {
+                ck[p] = k;
+                ca[p] = ra;
+                cb[p] = rb;
+            } else {
+                atomicOr(&ctl->err, ERR_CAPACITY);
+            }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((u64 *)&ctl->edges, (u64)nb);
+}
+
+// Delete, step 1: normalisation (absent edges and repeats dropped), removal
+// from the index and the CSR, and the tree-edge cut of Algorithm 1: for a
+// deleted edge {u, v} with parent[u] == v, parent[u] <- u (either
+// orientation).  The old root of a cut tree is stamped "affected"; the cut
+// vertex becomes a piece root and is stamped in cut_ep.
+__global__ void k_del_claim(const int *batch, long long len, Index ix, Csr g, u64 *ovf, int *parent,
+                            const int *rep, Ctl *ctl, unsigned *aff_ep, unsigned *cut_ep, int *cutlist) {
+    if (*(volatile int *)&ctl->skip) return;
+    unsigned ep = ctl->epoch;
+    GS_LOOP(i, len) {
+        int u = batch[2 * i], v = batch[2 * i + 1];
+        bool won = false;
+        int c = -1;
+        if (u != v) {
+            u64 key = ekey((uint32_t)u, (uint32_t)v);
+            long long s = index_find(ix, key);
+            if (s >= 0) won = atomicCAS(&ix.key[s], key, TOMB_KEY) == key;
+            if (won) {
+                uint32_t pu = ix.pu[s], pv = ix.pv[s];
+                if (pu == POS_OVF) {
+                    ovf[pv] = TOMB_KEY;
+                } else {
+                    g.col[pu] = -1;
+                    g.col[pv] = -1;
+                }
+                if (parent[u] == v) c = u;
+                else if (parent[v] == u) c = v;
+                if (c >= 0) {
+                    parent[c] = c;
+                    cut_ep[c] = ep;
+                    aff_ep[rep[c]] = ep;
+                }
+            }
+        }
+        agg_count(&ctl->self_loops, u == v);
+        agg_count(&ctl->dropped, u != v && !won);
+        agg_count(&ctl->htomb, won);
+        agg_count(&ctl->edges, won, -1);
+        agg_append(&ctl->nb, won);
+        long long p = agg_append(&ctl->ncut, c >= 0);
+        if (c >= 0) cutlist[p] = c;
+    }
+}
+
+// Delete, cross-edge scan (key edges M = E(G) - E(F) - B, Algorithm 1,
+// restricted): one warp per detached vertex u (rep changed by the cut)
+// streams u's row; a live neighbour x in another piece makes the candidate
+// {u, x}.  Every cross edge has at least one detached endpoint (the trees of
+// F spanned the components of G); when both are detached the smaller id
+// emits it, so each cross edge appears once.
+__global__ void k_scan_rows(const int *D, Ctl *ctl, Csr g, const int *rep, const unsigned *cut_ep, u64 *ck,
+                            int *ca, int *cb, u64 cand_cap) {
+    if (*(volatile int *)&ctl->skip) return;
+    long long nd = (long long)ctl->ndet;
+    unsigned ep = ctl->epoch;
+    int lane = threadIdx.x & 31;
+    long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    long long scanned = 0;
+    for (long long w = warp; w < nd; w += nw) {
+        int u = D[w];
+        int ru = rep[u];
+        long long o = g.off[u];
+        long long cap = g.off[u + 1] - o;
+        long long used = g.used[u];
+        if (used > cap) used = cap;
+        scanned += used;
+        for (long long j0 = 0; j0 < used; j0 += 32) {
+            long long j = j0 + lane;
+            bool emit = false;
+            int x = -1, rx = -1;
+            if (j < used) {
+                x = __ldcs(&g.col[o + j]);
+                if (x >= 0) {
+                    rx = rep[x];
+                    if (rx != ru) emit = cut_ep[rx] != ep || u < x;
+                }
+            }
+            long long p = agg_append(&ctl->ncand, emit);
+            if (emit) {
+                if ((u64)p < cand_cap) {
+                    ck[p] = ekey((uint32_t)u, (uint32_t)x);
+                    ca[p] = ru;
+                    cb[p] = rx;
+                } else {
+                    atomicOr(&ctl->err, ERR_CAPACITY);
+                }
+            }
+        }
+    }
+    if (lane == 0 && scanned) atomicAdd((u64 *)&ctl->scanned, (u64)scanned);
+}
+
+// Delete, cross-edge scan of the overflow list (edges outside their rows).
+__global__ void k_scan_ovf(const u64 *ovf, Ctl *ctl, const int *rep, u64 *ck, int *ca, int *cb, u64 cand_cap) {
+    if (*(volatile int *)&ctl->skip) return;
+    long long no = (long long)ctl->ovf_count;
+    GS_LOOP(i, no) {
+        u64 k = ovf[i];
+        bool emit = false;
+        int ra = -1, rb = -1;
+        if (k != TOMB_KEY) {
+            ra = rep[klo(k)];
+            rb = rep[khi(k)];
+            emit = ra != rb;
+        }
+        long long p = agg_append(&ctl->ncand, emit);
+        if (emit) {
+            if ((u64)p < cand_cap) {
+                ck[p] = k;
+                ca[p] = ra;
+                cb[p] = rb;
+            } else {
+                atomicOr(&ctl->err, ERR_CAPACITY);
+            }
+        }
+    }
+}
+
+// Edge-list export (rebuild and drsf_export_edges): warp per row, pairs
+// (u, x) with u < x, then the live overflow edges.
+__global__ void k_extract(int n, Csr g, const u64 *ovf, const Ctl *ctl, int *out, long long cap, u64 *cnt,
+                          int *bad) {
+    int lane = threadIdx.x & 31;
+    long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long u = warp; u < n; u += nw) {
+        long long o = g.off[u];
+        long long c = g.off[u + 1] - o;
+        long long used = g.used[u];
+        if (used > c) used = c;
+        for (long long j0 = 0; j0 < used; j0 += 32) {
+            long long j = j0 + lane;
+            int x = j < used ? g.col[o + j] : -1;
+            bool emit = x > (int)u;
+            long long p = agg_append(cnt, emit);
+            if (emit) {
+                if (p < cap) {
+                    out[2 * p] = (int)u;
+                    out[2 * p + 1] = x;
+                } else {
+                    atomicOr(bad, 1);
+                }
+            }
+        }
+    }
+    long long no = (long long)ctl->ovf_count;
+    GS_LOOP(i, no) {
+        u64 k = ovf[i];
+        bool emit = k != TOMB_KEY;
+        long long p = agg_append(cnt, emit);
+        if (emit) {
+            if (p < cap) {
+                out[2 * p] = (int)klo(k);
+                out[2 * p + 1] = (int)khi(k);
+            } else {
+                atomicOr(bad, 1);
+            }
+        }
+    }
+}
+
+// DRSF_VALIDATE: every parent pointer must be an edge of G.
+__global__ void k_check_tree_edges(int n, const int *parent, Index ix, int *bad) {
+    GS_LOOP(v, n) {
+        int p = parent[v];
+        if (p != (int)v && index_find(ix, ekey((uint32_t)v, (uint32_t)p)) < 0) atomicOr(bad, 2);
+    }
+}
+
+// DRSF_VALIDATE: no edge of G joins two different trees (one root per
+// component, given acyclic pointers along edges of G).
+__global__ void k_check_cross(const int *pairs, long long m, const int *rep, int *bad) {
+    GS_LOOP(i, m) {
+        if (rep[pairs[2 * i]] != rep[pairs[2 * i + 1]]) atomicOr(bad, 4);
+    }
+}
+
+// ------------------------------------------------------------- wrappers
+
+static unsigned gsz(long long n) { return grid_for(n, BLK, 152u * 16u); }
+
+cudaError_t launch_check_range(const int *a, long long cnt, int n, int *bad, cudaStream_t s) {
+    k_check_range<<<gsz(cnt), BLK, 0, s>>>(a, cnt, n, bad);
+    return cudaGetLastError();
+}
+cudaError_t launch_create_claim(const int *edges, long long m, Index ix, u64 *dkey, u64 *dslot, u64 *cnt,
+                                long long *self_loops, cudaStream_t s) {
+    k_create_claim<<<gsz(m), BLK, 0, s>>>(edges, m, ix, dkey, dslot, cnt, self_loops);
+    return cudaGetLastError();
+}
+cudaError_t launch_degree(const u64 *dkey, long long m, int *deg, cudaStream_t s) {
+    k_degree<<<gsz(m), BLK, 0, s>>>(dkey, m, deg);
+    return cudaGetLastError();
+}
+cudaError_t launch_caps(const int *deg, int n, long long *cap, cudaStream_t s) {
+    k_caps<<<gsz(n), BLK, 0, s>>>(deg, n, cap);
+    return cudaGetLastError();
+}
+cudaError_t launch_scan_i64(const long long *in, long long *out, long long n, long long *bsum, cudaStream_t s) {
+    long long tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (tiles < 1) tiles = 1;
+    k_scan_tiles<<<(unsigned)tiles, BLK, 0, s>>>(in, n, bsum);
+    k_scan_sums<<<1, BLK, 0, s>>>(bsum, tiles);
+    k_scan_apply<<<(unsigned)tiles, BLK, 0, s>>>(in, out, n, bsum);
+    return cudaGetLastError();
+}
+cudaError_t launch_fill(const u64 *dkey, const u64 *dslot, long long m, Csr g, Index ix, cudaStream_t s) {
+    k_fill<<<gsz(m), BLK, 0, s>>>(dkey, dslot, m, g, ix);
+    return cudaGetLastError();
+}
+cudaError_t launch_validate_batch(const int *batch, long long len, int n, Ctl *ctl, cudaStream_t s) {
+    if (len <= 0) return cudaSuccess;
+    k_validate_batch<<<gsz(2 * len), BLK, 0, s>>>(batch, len, n, ctl);
+    return cudaGetLastError();
+}
+cudaError_t launch_ins_claim(const int *batch, long long len, Index ix, Ctl *ctl, u64 *nkey, u64 *nslot,
+                             cudaStream_t s) {
+    if (len <= 0) return cudaSuccess;
+    k_ins_claim<<<gsz(len), BLK, 0, s>>>(batch, len, ix, ctl, nkey, nslot);
+    return cudaGetLastError();
+}
+cudaError_t launch_ins_place(const Dev &d, const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, Index ix,
+                             u64 *ovf, u64 ovf_cap, const int *rep, u64 *ck, int *ca, int *cb, u64 cand_cap,
+                             cudaStream_t s) {
+    k_ins_place<<<d.grid, BLK, 0, s>>>(nkey, nslot, ctl, g, ix, ovf, ovf_cap, rep, ck, ca, cb, cand_cap);
+    return cudaGetLastError();
+}
+cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u64 *ovf, int *parent,
+                             const int *rep, Ctl *ctl, unsigned *aff_ep, unsigned *cut_ep, int *cutlist,
+                             cudaStream_t s) {
+    if (len <= 0) return cudaSuccess;
+    k_del_claim<<<gsz(len), BLK, 0, s>>>(batch, len, ix, g, ovf, parent, rep, ctl, aff_ep, cut_ep, cutlist);
+    return cudaGetLastError();
+}
+cudaError_t launch_scan_rows(const Dev &d, const int *D, Ctl *ctl, Csr g, const int *rep,
+                             const unsigned *cut_ep, u64 *ck, int *ca, int *cb, u64 cand_cap, cudaStream_t s) {
+    k_scan_rows<<<d.grid, BLK, 0, s>>>(D, ctl, g, rep, cut_ep, ck, ca, cb, cand_cap);
+    return cudaGetLastError();
+}
+cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, u64 *ck, int *ca, int *cb,
+                            u64 cand_cap, cudaStream_t s) {
+    k_scan_ovf<<<d.nsm * 2, BLK, 0, s>>>(ovf, ctl, rep, ck, ca, cb, cand_cap);
+    return cudaGetLastError();
+}
+cudaError_t launch_extract(const Dev &d, int n, Csr g, const u64 *ovf, u64 novf_max, Ctl *ctl, int *out,
+                           long long cap, u64 *cnt, cudaStream_t s) {
+    (void)novf_max;
+    k_extract<<<d.grid, BLK, 0, s>>>(n, g, ovf, ctl, out, cap, cnt, (int *)(cnt + 1));
+    return cudaGetLastError();
+}
+cudaError_t launch_check_tree_edges(int n, const int *parent, Index ix, int *bad, cudaStream_t s) {
+    k_check_tree_edges<<<gsz(n), BLK, 0, s>>>(n, parent, ix, bad);
+    return cudaGetLastError();
+}
+cudaError_t launch_check_cross(const int *pairs, long long m, const int *rep, int *bad, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    k_check_cross<<<gsz(m), BLK, 0, s>>>(pairs, m, rep, bad);
+    return cudaGetLastError();
+}

@@ -1,0 +1,79 @@
+// Launch wrappers of the D-RSF kernels (host side).  Each wrapper enqueues
+// on `s` and returns the launch status.
+#pragma once
+
+#include "common.cuh"
+
+// Fixed launch shapes.
+#define BLK 256
+
+struct Dev {
+    int nsm;
+    unsigned grid;        // grid-stride kernels: nsm * 8 blocks of BLK
+    unsigned coop_jump;   // cooperative kernels: co-resident block counts
+    unsigned coop_hook;
+    unsigned coop_orient;
+    unsigned coop_mark;
+};
+
+// graph.cu -------------------------------------------------------------
+cudaError_t launch_check_range(const int *a, long long cnt, int n, int *bad, cudaStream_t s);
+cudaError_t launch_create_claim(const int *edges, long long m, Index ix, u64 *dkey, u64 *dslot, u64 *cnt,
+                                long long *self_loops, cudaStream_t s);
+cudaError_t launch_degree(const u64 *dkey, long long m, int *deg, cudaStream_t s);
+cudaError_t launch_caps(const int *deg, int n, long long *cap, cudaStream_t s);
+cudaError_t launch_scan_i64(const long long *in, long long *out, long long n, long long *bsum, cudaStream_t s);
+cudaError_t launch_fill(const u64 *dkey, const u64 *dslot, long long m, Csr g, Index ix, cudaStream_t s);
+cudaError_t launch_validate_batch(const int *batch, long long len, int n, Ctl *ctl, cudaStream_t s);
+cudaError_t launch_ins_claim(const int *batch, long long len, Index ix, Ctl *ctl, u64 *nkey, u64 *nslot,
+                             cudaStream_t s);
+cudaError_t launch_ins_place(const Dev &d, const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, Index ix,
+                             u64 *ovf, u64 ovf_cap, const int *rep, u64 *ck, int *ca, int *cb, u64 cand_cap,
+                             cudaStream_t s);
+cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u64 *ovf, int *parent,
+                             const int *rep, Ctl *ctl, unsigned *aff_ep, unsigned *cut_ep, int *cutlist,
+                             cudaStream_t s);
+cudaError_t launch_scan_rows(const Dev &d, const int *D, Ctl *ctl, Csr g, const int *rep,
+                             const unsigned *cut_ep, u64 *ck, int *ca, int *cb, u64 cand_cap, cudaStream_t s);
+cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, u64 *ck, int *ca, int *cb,
+                            u64 cand_cap, cudaStream_t s);
+cudaError_t launch_extract(const Dev &d, int n, Csr g, const u64 *ovf, u64 novf_max, Ctl *ctl, int *out,
+                           long long cap, u64 *cnt, cudaStream_t s);
+cudaError_t launch_check_tree_edges(int n, const int *parent, Index ix, int *bad, cudaStream_t s);
+cudaError_t launch_check_cross(const int *pairs, long long m, const int *rep, int *bad, cudaStream_t s);
+
+// forest.cu ------------------------------------------------------------
+cudaError_t launch_begin(Ctl *ctl, int op, long long len, cudaStream_t s);
+cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, const int *parent,
+                               int *J0, int *A, Ctl *ctl, cudaStream_t s);
+cudaError_t launch_copy_parent(int n, const int *parent, int *J0, cudaStream_t s);
+cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J0,
+                        int *J1, int *rep, int *D, int mode, cudaStream_t s);
+cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
+                           int *comp, u64 *best0, u64 *best1, u64 *er, long long er_cap, cudaStream_t s);
+struct OrientArgs {
+    const u64 *er;
+    const int *rep;
+    int *comp, *minp, *pidx, *plist;
+    unsigned *pstamp;
+    int *pdeg, *pcur, *poff, *adj, *apos;
+    int *val0, *val1, *nx0, *nx1;
+    long long *bsum;
+    int *chx, *chy;
+    unsigned *att_ep, *rep_ep;
+    int *att_x, *newrep;
+};
+cudaError_t launch_orient(const Dev &d, Ctl *ctl, OrientArgs a, cudaStream_t s);
+cudaError_t launch_active(const Dev &d, const int *L, int use_list, long long cnt_static, Ctl *ctl, int *rep,
+                          const int *parent, const unsigned *att_ep, const int *att_x, const unsigned *rep_ep,
+                          const int *newrep, int *act, int *pold, int *J0, unsigned char *mark, cudaStream_t s);
+cudaError_t launch_mark(const Dev &d, Ctl *ctl, const int *act, int *J0, int *J1, unsigned char *mark,
+                        const int *parent, cudaStream_t s);
+cudaError_t launch_reverse(const Dev &d, Ctl *ctl, const int *act, const int *pold, const unsigned char *mark,
+                           const int *chx, const int *chy, int *parent, cudaStream_t s);
+cudaError_t launch_labels(int n, const int *rep, int *tmp, int *out, cudaStream_t s);
+
+unsigned coop_blocks_jump(int nsm);
+unsigned coop_blocks_hook(int nsm);
+unsigned coop_blocks_orient(int nsm);
+unsigned coop_blocks_mark(int nsm);

@@ -1,0 +1,168 @@
+"""GPU parity: the CUDA path against the serial oracle, batch by batch.
+
+Bar: the parent array equals the oracle's bit for bit (deterministic mode:
+minimum-key replacement edges, smallest-root super-roots), the labels equal
+the oracle's component minima, the exact checker accepts the forest, and the
+per-batch counters agree.  Integer work only, so every comparison is exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2607_20211_gb300 as drsf
+import workloads
+from tests.gpu_util import check_batch, dev_tensor, make_forest, run_trajectory
+
+pytestmark = pytest.mark.gpu
+
+I, D = drsf.INSERT, drsf.DELETE
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    drsf.build()
+
+
+def test_er_small_config():
+    """Erdos-Renyi n=20,000, m=25,000 (seed 1): one insert batch of 2,000 new
+    pairs, then one delete batch of 2,000 edges (half tree edges)."""
+    g = workloads.er_graph(20_000, 25_000, seed=1)
+    run_trajectory(g, [(I, 2000), (D, 2000)], seed=1)
+
+
+def test_er_multi_batch():
+    g = workloads.er_graph(20_000, 25_000, seed=11)
+    run_trajectory(g, [(I, 3000), (D, 3000)] * 4, seed=12)
+
+
+def test_rmat16_trajectory():
+    g = workloads.rmat_graph(16, 16, seed=2)
+    run_trajectory(g, [(I, 1000), (D, 1000), (I, 10_000), (D, 10_000)] * 3, seed=3)
+
+
+def test_grid_deep_paths():
+    """Grid 512 x 512, p = 0.6, deletes with 90% tree edges (long reversals),
+    local inserts within 64 cells."""
+    g = workloads.grid_graph(512, 512, seed=3)
+    st = run_trajectory(g, [(D, 5000), (I, 5000)] * 3, seed=4, tree_frac=0.9, local=64)
+    assert st is not None
+
+
+def test_deterministic_run_to_run():
+    g = workloads.rmat_graph(14, 8, seed=5)
+    tr = workloads.Trajectory(g, seed=6)
+    b1 = tr.next_batch(D, 3000)
+    outs = []
+    for _ in range(2):
+        f = make_forest(g)
+        f.apply(D, dev_tensor(b1))
+        outs.append(f.parent().cpu().numpy())
+        f.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def _tiny(n, edges, parent):
+    keys = workloads.edges_to_keys(np.array(edges, np.int64).reshape(-1, 2)) if edges else np.zeros(0, np.uint64)
+    g = workloads.Graph.__new__(workloads.Graph)
+    g.name, g.n, g.keys, g.W = "tiny", n, keys, 0
+    g.parent = np.array(parent, np.int32) if parent is not None else workloads.bfs_forest(n, keys)
+    return g
+
+
+def test_edge_cases():
+    # n = 1, empty graph, empty batch and a self-loop
+    g = _tiny(1, [], [0])
+    f = make_forest(g)
+    for op, b in [(I, np.zeros((0, 2), np.int32)), (I, np.array([[0, 0]], np.int32)),
+                  (D, np.array([[0, 0]], np.int32))]:
+        check_batch(f, 1, g.keys, g.parent, op, b)
+    f.close()
+    # star, then duplicates / existing / absent / self-loops
+    n = 50
+    g = _tiny(n, [(0, i) for i in range(1, n)], None)
+    f = make_forest(g)
+    keys, par = g.keys, g.parent
+    b = np.array([[3, 3], [1, 2], [2, 1], [0, 5], [7, 9], [9, 7], [9, 7]], np.int32)
+    keys, par, st = check_batch(f, n, keys, par, I, b)
+    b = np.array([[0, 5], [5, 0], [4, 6], [1, 2], [0, 1], [8, 8]], np.int32)
+    keys, par, st = check_batch(f, n, keys, par, D, b)
+    # delete every tree edge of the star: all leaves become singletons or re-hang
+    b = np.array([[0, i] for i in range(1, n)], np.int32)
+    keys, par, st = check_batch(f, n, keys, par, D, b)
+    f.close()
+    # insert into an edgeless graph (pure Kruskal)
+    n = 3000
+    g = _tiny(n, [], list(range(n)))
+    f = make_forest(g)
+    rng = np.random.default_rng(1)
+    check_batch(f, n, g.keys, g.parent, I, rng.integers(0, n, (5000, 2)).astype(np.int32))
+    f.close()
+
+
+def test_long_path_reversal():
+    """A single path of 200,000 vertices rooted at 0 plus the closing edge;
+    deleting the first tree edge re-roots the whole path (depth n - 1)."""
+    n = 200_000
+    edges = [(i, i + 1) for i in range(n - 1)] + [(0, n - 1)]
+    g = _tiny(n, edges, [0] + list(range(n - 1)))
+    f = make_forest(g)
+    keys, par, st = check_batch(f, n, g.keys, g.parent, D, np.array([[1, 0]], np.int32))
+    assert st["reversed"] == n - 2
+    # and several cuts at once along the path
+    b = np.array([[k, k + 1] for k in range(5000, n - 1, 17_000)], np.int32)
+    check_batch(f, n, keys, par, D, b)
+    f.close()
+
+
+def test_invalid_id_skips_batch():
+    g = workloads.er_graph(1000, 1500, seed=7)
+    f = make_forest(g)
+    before = f.parent().cpu().numpy()
+    f.apply(I, dev_tensor(np.array([[0, 1], [2, 1000]], np.int32)))
+    with pytest.raises(drsf.DRSFError) as e:
+        f.sync()
+    assert e.value.status == drsf.EINVAL
+    assert np.array_equal(f.parent().cpu().numpy(), before)
+    assert f.num_edges() == g.m
+    # the handle stays usable
+    tr = workloads.Trajectory(g, seed=8)
+    check_batch(f, g.n, g.keys, g.parent, I, tr.next_batch(I, 100))
+    f.close()
+
+
+def test_apply_host_matches_device():
+    g = workloads.rmat_graph(14, 8, seed=9)
+    tr = workloads.Trajectory(g, seed=10)
+    b = tr.next_batch(D, 2000)
+    f1, f2 = make_forest(g), make_forest(g)
+    f1.apply(D, dev_tensor(b))
+    f2.apply_host(D, b)
+    assert np.array_equal(f1.parent().cpu().numpy(), f2.parent().cpu().numpy())
+    f1.close()
+    f2.close()
+
+
+def test_overflow_and_rebuild():
+    """Rows fill past their slack (edges spill to the overflow list) and the
+    index fills past its load limit (storage rebuild), with parity kept."""
+    g = workloads.er_graph(4000, 4000, seed=13)
+    st = run_trajectory(g, [(I, 60_000)] * 4 + [(D, 30_000), (I, 40_000), (D, 50_000)], seed=14,
+                        labels=True)
+    assert st["rebuilds"] >= 1
+
+
+def test_validate_flag():
+    g = workloads.er_graph(500, 800, seed=15)
+    f = make_forest(g, flags=drsf.DETERMINISTIC | drsf.VALIDATE)
+    f.close()
+    bad = g.parent.copy()
+    roots = np.nonzero(bad == np.arange(g.n))[0]
+    # give a root a parent that is not its neighbour
+    r = int(roots[0])
+    bad[r] = (r + 1) % g.n if (r + 1) % g.n != r else r
+    with pytest.raises(drsf.DRSFError) as e:
+        drsf.DynamicForest(g.n, dev_tensor(g.edges()), dev_tensor(bad), flags=drsf.VALIDATE)
+    assert e.value.status in (drsf.ENOT_FOREST,)
