@@ -1,0 +1,441 @@
+#!/usr/bin/env python
+"""Benchmark of the D-RSF batch update on one GB300.
+
+Workload (default): R-MAT scale 22, edge factor 16, Graph500 initiator
+(0.57, 0.19, 0.19, 0.05), ids permuted, seed 5 (4,194,304 vertices, ~64M
+undirected edges, synthetic stand-in for the paper's Kronecker graphs); the
+initial forest is the FIFO-BFS forest from each component's smallest id.
+One step = one 100K-edge insert batch (uniform new pairs) followed by one
+100K-edge delete batch (50% tree edges of the current forest, 50% non-tree
+edges), applied through the C ABI.  Metric: updates/s = applied updates per
+second over exactly K timed steps (CUDA events, L2 flushed between steps).
+
+The batches follow one trajectory: an untimed planning pass on the GPU
+generates each batch from the current graph and forest, then a fresh handle
+replays the same batches for timing (the update is deterministic, so the
+timed run sees the same states; the final parent arrays are compared).
+
+Prints one JSON line (rank 0).  --impl reference times the serial CPU oracle
+on the same workload instead.  With --gpus N > 1 (torchrun) every rank runs
+an independent replica (the update of one graph does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "updates/s (insert + delete, R-MAT scale 22, 100K-update batches)"
+UNIT = "updates/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="rmat22",
+                   choices=["rmat22", "rmat20", "grid4096", "er-small"])
+    p.add_argument("--batch", type=int, default=0, help="batch size (default per workload)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------ workloads
+
+def make_graph(name):
+    import workloads
+    if name == "rmat22":
+        return workloads.rmat_graph(22, 16, seed=5), dict(tree_frac=0.5, local=0, batch=100_000)
+    if name == "rmat20":
+        return workloads.rmat_graph(20, 16, seed=2), dict(tree_frac=0.5, local=0, batch=100_000)
+    if name == "grid4096":
+        return workloads.grid_graph(4096, 4096, seed=3), dict(tree_frac=0.9, local=64, batch=100_000)
+    return workloads.er_graph(20_000, 25_000, seed=1), dict(tree_frac=0.5, local=0, batch=2000)
+
+
+def workload_config(name, g, b):
+    desc = {
+        "rmat22": "R-MAT scale 22, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), ids permuted, seed 5",
+        "rmat20": "R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), ids permuted, seed 2",
+        "grid4096": "4096x4096 grid, p=0.6, 0.1% shortcuts, seed 3; deletes 90% tree, inserts within 64 cells",
+        "er-small": "Erdos-Renyi n=20,000 m=25,000 seed 1",
+    }[name]
+    return {"workload": desc, "vertices": int(g.n), "edges": int(g.m), "batch": int(b),
+            "step": f"one {b}-edge insert batch + one {b}-edge delete batch",
+            "initial_forest": "FIFO BFS from each component's smallest id",
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
+# ------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        load = [r for r in rows if r[2] > 0.3 * max(x[2] for x in rows)] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ distributed
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch.distributed as dist
+    rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, local
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def aggregate(units: float, seconds: float):
+    """Whole-job throughput: units summed over ranks / slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return units, seconds
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([units, seconds], dtype=torch.float64, device=dev)
+    u = t[:1].clone()
+    s = t[1:].clone()
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(s.item())
+
+
+# ------------------------------------------------------------ algorithmic bytes
+
+def phase_bytes(st: dict, n: int, op: int) -> dict:
+    """Algorithmic bytes per phase of one batch: each data item a phase must
+    touch, counted once per pass (see the design notes for the model)."""
+    b, a = st["batch_len"], st["applied"]
+    out = {"begin": 8 * b}
+    if op == 0:
+        c = st["candidates"]
+        out["ins_claim"] = 8 * b + 8 * b + 16 * a
+        out["ins_place"] = 80 * a + 16 * c
+        out["active"] = 12 * n + 16 * st["active"]
+    else:
+        aff, det, sc, c = st["affected"], st["detached"], st["scanned"], st["candidates"]
+        out["del_claim"] = 8 * b + 40 * a + 12 * st["tree_cut"]
+        out["affected"] = 8 * n + 12 * aff
+        out["jump"] = 16 * aff * max(st["jump_rounds"], 1) + 16 * aff + 4 * det
+        out["scan"] = 28 * det + 8 * sc + 20 * c
+        out["active"] = 16 * aff + 16 * st["active"]
+    c, ner = st["candidates"], st["replacement"]
+    out["hook"] = 80 * c + 16 * ner
+    out["orient"] = 120 * ner + 32 * ner * max(st["rank_rounds"], 1)
+    out["mark"] = 22 * st["active"] * max(st["mark_rounds"], 1)
+    out["reverse"] = 18 * st["active"] + 4 * st["reversed"] + 8 * ner
+    return out
+
+
+def ncu_traffic(kernel_phase: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken
+    on the current source of that kernel."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path)).get(kernel_phase)
+        if not d:
+            return None
+        src = os.path.join(ROOT, d["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return d["bytes_per_launch"] if sha == d["source_sha"] else None
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------ our arm
+
+def plan(g, cfg, steps, b, seed):
+    """Untimed pass on the GPU that generates the trajectory's batches."""
+    import torch
+    import paper_2607_20211_gb300 as drsf
+    import workloads
+    f = drsf.DynamicForest(g.n, torch.from_numpy(g.edges()).cuda(), torch.from_numpy(g.parent).cuda())
+    tr = workloads.Trajectory(g, seed, tree_frac=cfg["tree_frac"], local=cfg["local"])
+    out = []
+    for _ in range(steps):
+        pair = []
+        for op in (0, 1):
+            batch = tr.next_batch(op, b)
+            f.apply(op, torch.from_numpy(batch).cuda())
+            st = f.stats()
+            par = f.parent().cpu().numpy()
+            tr.advance(batch, op, par)
+            pair.append((batch, st))
+        out.append(pair)
+    final = f.parent().cpu().numpy()
+    f.close()
+    return out, final
+
+
+def run_ours(args, rank, ws, local):
+    import torch
+    import paper_2607_20211_gb300 as drsf
+    torch.cuda.set_device(local)
+    drsf.build()
+    g, cfg = make_graph(args.workload)
+    b = args.batch or cfg["batch"]
+    K, W = args.steps, args.warmup
+    steps, final_plan = plan(g, cfg, W + K, b, seed=5)
+    dev_batches = [[torch.from_numpy(p[0]).cuda() for p in s] for s in steps]
+    edges_d = torch.from_numpy(g.edges()).cuda()
+    parent_d = torch.from_numpy(g.parent).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    f = drsf.DynamicForest(g.n, edges_d, parent_d)
+    for s in range(W):
+        for op in (0, 1):
+            f.apply(op, dev_batches[s][op])
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    f.profile_start(2 * K + 4)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record(stream)
+        f.apply(0, dev_batches[W + k][0])
+        ev[k][1].record(stream)
+        f.apply(1, dev_batches[W + k][1])
+        ev[k][2].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    prof = f.profile_stop()
+    final = f.parent().cpu().numpy()
+    f.close()
+    if not np.array_equal(final, final_plan):
+        raise RuntimeError("timed replay diverged from the planning pass")
+    ins_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    del_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
+    step_ms = [i + d for i, d in zip(ins_ms, del_ms)]
+    applied_i = sum(steps[W + k][0][1]["applied"] for k in range(K))
+    applied_d = sum(steps[W + k][1][1]["applied"] for k in range(K))
+    total_s = sum(step_ms) / 1e3
+    units, secs = aggregate(float(applied_i + applied_d), total_s)
+
+    # roofline of the dominant phase (kernel), from live events + the
+    # algorithmic byte model over the same K steps
+    pbytes = {}
+    for k in range(K):
+        for op in (0, 1):
+            for ph, by in phase_bytes(steps[W + k][op][1], g.n, op).items():
+                pbytes[ph] = pbytes.get(ph, 0) + by
+    phases = {ph: v for ph, v in prof.items() if ph != "batches"}
+    dom = max(phases, key=lambda p: phases[p][0])
+    dom_ms, dom_launch = phases[dom]
+    per_launch_bytes = pbytes.get(dom, 0) / max(dom_launch, 1)
+    per_launch_ms = dom_ms / max(dom_launch, 1)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": ncu_traffic(dom),
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "algorithmic_bytes_per_launch": int(per_launch_bytes),
+                "ms_per_launch": round(per_launch_ms, 5)}
+    step_total_ms = sum(v[0] for v in phases.values())
+    phase_table = {p: {"ms_per_step": round(v[0] / K, 4), "share": round(v[0] / step_total_ms, 4),
+                       "launches": int(v[1]),
+                       "GBps": round(pbytes.get(p, 0) / (v[0] / 1e3) / 1e9, 1) if v[0] > 0 else None}
+                   for p, v in phases.items() if v[1] > 0}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        f = drsf.DynamicForest(g.n, edges_d, parent_d)
+        host = [[np.ascontiguousarray(p[0]) for p in s] for s in steps]
+        for s in range(W):
+            for op in (0, 1):
+                f.apply_host(op, host[s][op])
+        f.stats()
+        barrier()
+        tt = 0.0
+        h2d = 0
+        for k in range(K):
+            t0 = time.perf_counter()
+            f.apply_host(0, host[W + k][0])
+            f.apply_host(1, host[W + k][1])
+            st = f.stats()   # device -> host read of the step's result counters
+            tt += time.perf_counter() - t0
+            h2d += host[W + k][0].nbytes + host[W + k][1].nbytes
+        barrier()
+        f.close()
+        eu, es = aggregate(float(applied_i + applied_d), tt)
+        e2e = {"value": round(eu / es, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d // K),
+               "d2h_bytes_per_step": 152, "ms_per_step": round(tt / K * 1e3, 4),
+               "path": "drsf_apply_host (pinned staging) + drsf_stats read-back"}
+    clocks = clk.stop()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(g, steps)
+    if rank != 0:
+        return
+    lat = sorted(ins_ms + del_ms)
+    line = {
+        "metric": METRIC if args.workload == "rmat22" else f"updates/s ({args.workload}, {b}-update batches)",
+        "value": round(units / secs, 1), "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": round(secs / K * 1e3, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {**workload_config(args.workload, g, b), "parallelism": "replicas" if ws > 1 else "single"},
+        "insert_updates_per_s": round(applied_i / (sum(ins_ms) / 1e3), 1),
+        "delete_updates_per_s": round(applied_d / (sum(del_ms) / 1e3), 1),
+        "batch_latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
+                             "p99": round(float(np.percentile(lat, 99)), 4),
+                             "insert_p50": round(float(np.median(ins_ms)), 4),
+                             "delete_p50": round(float(np.median(del_ms)), 4)},
+        "roofline": roofline, "phases": phase_table, "e2e": e2e, "cpu_baseline": cpu,
+        "gpu_launches": int(sum(v[1] for v in phases.values())),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(g, steps):
+    """The serial oracle on the host cores, one step of the same trajectory
+    (the first insert + delete batch from the initial state)."""
+    import oracle
+    keys, par = g.keys, g.parent
+    t = 0.0
+    applied = 0
+    for op in (0, 1):
+        batch = steps[0][op][0]
+        t0 = time.perf_counter()
+        r = oracle.apply(g.n, keys, par, op, batch, want_keys=True)
+        t += time.perf_counter() - t0
+        applied += r.stats["applied"]
+        keys, par = r.keys, r.parent
+    return {"value": round(applied / t, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 step (insert + delete, {len(steps[0][0][0])} edges each) of the same trajectory",
+            "seconds": round(t, 3)}
+
+
+# ------------------------------------------------------------ reference arm
+
+def run_reference(args, rank, ws):
+    """The serial oracle as the reference arm: each step applies one batch of
+    the trajectory (alternating insert / delete) on the host."""
+    if rank != 0:
+        return
+    import oracle
+    import workloads
+    g, cfg = make_graph(args.workload)
+    b = args.batch or cfg["batch"]
+    tr = workloads.Trajectory(g, 5, tree_frac=cfg["tree_frac"], local=cfg["local"])
+    keys, par = g.keys, g.parent
+    t = 0.0
+    applied = 0
+    for s in range(args.warmup + args.steps):
+        op = s % 2
+        batch = tr.next_batch(op, b)
+        t0 = time.perf_counter()
+        r = oracle.apply(g.n, keys, par, op, batch, want_keys=True)
+        dt = time.perf_counter() - t0
+        keys, par = r.keys, r.parent
+        tr.keys, tr.parent = keys, par
+        if s >= args.warmup:
+            t += dt
+            applied += r.stats["applied"]
+    v = round(applied / t, 1)
+    line = {"impl": "reference",
+            "metric": METRIC if args.workload == "rmat22" else f"updates/s ({args.workload}, {b}-update batches)",
+            "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {**workload_config(args.workload, g, b), "parallelism": "single",
+                       "reference_step": "one batch (alternating insert / delete) through the serial oracle"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": 1,
+                             "sample": f"{args.steps} batches of {b} edges, alternating insert/delete"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, ws, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+    else:
+        run_ours(args, rank, ws, local)
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

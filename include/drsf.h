@@ -187,6 +187,24 @@ DRSF_API int64_t drsf_num_edges(drsf_handle h, drsf_stream stream);
  * *m_out receives the number of edges.  Synchronises. */
 DRSF_API drsf_status drsf_export_edges(drsf_handle h, int32_t *out, int64_t cap, int64_t *m_out, drsf_stream stream);
 
+/*
+ * Per-phase timing (instrumentation; not part of the paper).  Between
+ * drsf_profile_start and drsf_profile_stop every drsf_apply brackets each
+ * phase of the update with CUDA events on its stream; stop synchronises and
+ * returns the summed device time and launch count of each phase over the
+ * profiled batches.  max_batches bounds the event pool (batches beyond it
+ * are not timed).  Phase names come from drsf_phase_name.
+ */
+#define DRSF_NUM_PHASES 12
+typedef struct {
+    double ms[DRSF_NUM_PHASES];        /* summed device time per phase */
+    int64_t launches[DRSF_NUM_PHASES]; /* kernel launches per phase */
+    int64_t batches;                   /* batches timed */
+} drsf_profile_t;
+DRSF_API drsf_status drsf_profile_start(drsf_handle h, int64_t max_batches);
+DRSF_API drsf_status drsf_profile_stop(drsf_handle h, drsf_profile_t *out, drsf_stream stream);
+DRSF_API const char *drsf_phase_name(int phase);
+
 /* drsf_destroy -- release all device memory (synchronises the handle's last
  * stream).  NULL is a no-op. */
 DRSF_API void drsf_destroy(drsf_handle h);

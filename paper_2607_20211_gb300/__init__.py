@@ -53,6 +53,14 @@ class BatchStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+NUM_PHASES = 12
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * NUM_PHASES), ("launches", ctypes.c_int64 * NUM_PHASES),
+                ("batches", ctypes.c_int64)]
+
+
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 _live_blocks: dict[int, torch.Tensor] = {}
@@ -117,6 +125,12 @@ def _load():
         lib.drsf_destroy.argtypes = [vp]
         lib.drsf_error_string.restype = ctypes.c_char_p
         lib.drsf_error_string.argtypes = [ctypes.c_int]
+        lib.drsf_profile_start.restype = ctypes.c_int
+        lib.drsf_profile_start.argtypes = [vp, i64]
+        lib.drsf_profile_stop.restype = ctypes.c_int
+        lib.drsf_profile_stop.argtypes = [vp, P(Profile), vp]
+        lib.drsf_phase_name.restype = ctypes.c_char_p
+        lib.drsf_phase_name.argtypes = [ctypes.c_int]
         _lib = lib
         return lib
 
@@ -247,6 +261,22 @@ class DynamicForest:
         if st:
             raise DRSFError(st, "drsf_export_edges")
         return out[:got.value]
+
+    def profile_start(self, max_batches: int) -> None:
+        """Start per-phase CUDA-event timing of the next batches."""
+        st = _lib.drsf_profile_start(self._h, int(max_batches))
+        if st:
+            raise DRSFError(st, "drsf_profile_start")
+
+    def profile_stop(self) -> dict:
+        """Stop timing; {phase: (ms, launches)} plus 'batches'."""
+        p = Profile()
+        st = _lib.drsf_profile_stop(self._h, ctypes.byref(p), _stream_ptr(self._stream))
+        if st:
+            raise DRSFError(st, "drsf_profile_stop")
+        out = {_lib.drsf_phase_name(i).decode(): (p.ms[i], p.launches[i]) for i in range(NUM_PHASES)}
+        out["batches"] = p.batches
+        return out
 
     def close(self) -> None:
         if getattr(self, "_h", None):

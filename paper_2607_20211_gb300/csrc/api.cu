@@ -75,7 +75,45 @@ struct drsf_ctx {
     long long ovf_bound = 0;     // overflow entries
     long long ctomb_bound = 0;   // deleted CSR entries
     long long rebuilds = 0;
+    // per-phase profiling
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;      // pairs per (batch, phase)
+    std::vector<int> prof_phase;           // phase of each pair
+    size_t prof_used = 0;                  // pairs used
+    long long prof_batches = 0;
+    long long prof_launch[DRSF_NUM_PHASES] = {0};
 };
+
+// Phases of one batch, in launch order.
+enum {
+    PH_BEGIN = 0,     // k_begin + id validation
+    PH_INS_CLAIM,     // insert: normalisation + index claim
+    PH_INS_PLACE,     // insert: CSR append + cross test
+    PH_DEL_CLAIM,     // delete: normalisation, removal, tree-edge cut
+    PH_AFF,           // delete: affected-vertex list
+    PH_JUMP,          // delete: pointer jumping (representatives)
+    PH_SCAN,          // delete: cross-edge scan of detached rows + overflow
+    PH_HOOK,          // hook-and-compress (replacement edges)
+    PH_ORIENT,        // Euler-tour orientation
+    PH_ACTIVE,        // path-reversal set-up + representative refresh
+    PH_MARK,          // pointer-doubling marks
+    PH_REVERSE        // reversal scatter + attach
+};
+static const char *kPhaseNames[DRSF_NUM_PHASES] = {
+    "begin", "ins_claim", "ins_place", "del_claim", "affected", "jump", "scan", "hook", "orient", "active",
+    "mark", "reverse"};
+
+static void prof_begin(drsf_ctx *h, int phase, cudaStream_t s) {
+    if (!h->prof_on || 2 * (h->prof_used + 1) > h->prof_ev.size()) return;
+    cudaEventRecord(h->prof_ev[2 * h->prof_used], s);
+    h->prof_phase[h->prof_used] = phase;
+}
+static void prof_end(drsf_ctx *h, int phase, int launches, cudaStream_t s) {
+    if (!h->prof_on || 2 * (h->prof_used + 1) > h->prof_ev.size()) return;
+    cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], s);
+    h->prof_launch[phase] += launches;
+    h->prof_used++;
+}
 
 // ------------------------------------------------------------- memory
 
@@ -392,6 +430,7 @@ static void destroy_all(drsf_ctx *h) {
     if (h->ctl_host) cudaFreeHost(h->ctl_host);
     if (h->stage_host) cudaFreeHost(h->stage_host);
     if (h->stage_done) cudaEventDestroy(h->stage_done);
+    for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
     delete h;
 }
 
@@ -507,25 +546,42 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
     if (st) return st;
     Ctl *ctl = h->ctl;
     Csr g{h->off, h->used, h->col};
+    if (h->prof_on) h->prof_batches++;
+    prof_begin(h, PH_BEGIN, s);
     CK(launch_begin(ctl, op, len, s));
     CK(launch_validate_batch(batch, len, h->n, ctl, s));
+    prof_end(h, PH_BEGIN, len > 0 ? 2 : 1, s);
     if (op == DRSF_INSERT) {
         // Algorithm 1, insert: F^ = F, M = B; rep of the previous batch is current
+        prof_begin(h, PH_INS_CLAIM, s);
         CK(launch_ins_claim(batch, len, h->ix, ctl, h->nkey, h->nslot, s));
+        prof_end(h, PH_INS_CLAIM, len > 0 ? 1 : 0, s);
+        prof_begin(h, PH_INS_PLACE, s);
         CK(launch_ins_place(h->dev, h->nkey, h->nslot, ctl, g, h->ix, h->ovf, h->ovf_cap, h->rep, h->ck[0],
                             h->ca[0], h->cb[0], h->cand_cap, s));
+        prof_end(h, PH_INS_PLACE, 1, s);
     } else {
         // Algorithm 1, delete: remove B, cut tree edges, re-label the cut trees
+        prof_begin(h, PH_DEL_CLAIM, s);
         CK(launch_del_claim(batch, len, h->ix, g, h->ovf, h->parent, h->rep, ctl, h->aff_ep, h->cut_ep,
                             h->cutlist, s));
+        prof_end(h, PH_DEL_CLAIM, len > 0 ? 1 : 0, s);
+        prof_begin(h, PH_AFF, s);
         CK(launch_aff_collect(h->dev, h->n, h->rep, h->aff_ep, h->parent, h->J0, h->A, ctl, s));
+        prof_end(h, PH_AFF, 1, s);
+        prof_begin(h, PH_JUMP, s);
         CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->J0, h->J1, h->rep, h->D, 1, s));
+        prof_end(h, PH_JUMP, 1, s);
+        prof_begin(h, PH_SCAN, s);
         CK(launch_scan_rows(h->dev, h->D, ctl, g, h->rep, h->cut_ep, h->ck[0], h->ca[0], h->cb[0], h->cand_cap,
                             s));
         CK(launch_scan_ovf(h->dev, h->ovf, ctl, h->rep, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
+        prof_end(h, PH_SCAN, 2, s);
     }
+    prof_begin(h, PH_HOOK, s);
     CK(launch_boruvka(h->dev, ctl, h->ck[0], h->ca[0], h->cb[0], h->ck[1], h->ca[1], h->cb[1], h->comp, h->best0,
                       h->best1, h->er, h->n, s));
+    prof_end(h, PH_HOOK, 1, s);
     OrientArgs oa{};
     oa.er = h->er;
     oa.rep = h->rep;
@@ -550,15 +606,23 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
     oa.rep_ep = h->rep_ep;
     oa.att_x = h->att_x;
     oa.newrep = h->newrep;
+    prof_begin(h, PH_ORIENT, s);
     CK(launch_orient(h->dev, ctl, oa, s));
+    prof_end(h, PH_ORIENT, 1, s);
+    prof_begin(h, PH_ACTIVE, s);
     if (op == DRSF_INSERT)
         CK(launch_active(h->dev, nullptr, 0, h->n, ctl, h->rep, h->parent, h->att_ep, h->att_x, h->rep_ep,
                          h->newrep, h->act, h->pold, h->J0, h->mark, s));
     else
         CK(launch_active(h->dev, h->A, 1, 0, ctl, h->rep, h->parent, h->att_ep, h->att_x, h->rep_ep, h->newrep,
                          h->act, h->pold, h->J0, h->mark, s));
+    prof_end(h, PH_ACTIVE, 1, s);
+    prof_begin(h, PH_MARK, s);
     CK(launch_mark(h->dev, ctl, h->act, h->J0, h->J1, h->mark, h->parent, s));
+    prof_end(h, PH_MARK, 1, s);
+    prof_begin(h, PH_REVERSE, s);
     CK(launch_reverse(h->dev, ctl, h->act, h->pold, h->mark, h->chx, h->chy, h->parent, s));
+    prof_end(h, PH_REVERSE, 2, s);
     return DRSF_OK;
 }
 
@@ -692,6 +756,43 @@ drsf_status drsf_export_edges(drsf_handle h, int32_t *out, int64_t cap, int64_t 
     hfree(h, &cnt, s);
     *m_out = (int64_t)hc[0];
     return ((int *)hc)[2] ? DRSF_EINVAL : DRSF_OK;
+}
+
+drsf_status drsf_profile_start(drsf_handle h, int64_t max_batches) {
+    if (!h || max_batches < 1) return DRSF_EINVAL;
+    set_dev(h);
+    size_t pairs = (size_t)max_batches * DRSF_NUM_PHASES;
+    while (h->prof_ev.size() < 2 * pairs) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        h->prof_ev.push_back(e);
+    }
+    h->prof_phase.assign(pairs, 0);
+    h->prof_used = 0;
+    h->prof_batches = 0;
+    for (int i = 0; i < DRSF_NUM_PHASES; ++i) h->prof_launch[i] = 0;
+    h->prof_on = true;
+    return DRSF_OK;
+}
+
+drsf_status drsf_profile_stop(drsf_handle h, drsf_profile_t *out, drsf_stream stream) {
+    if (!h || !out) return DRSF_EINVAL;
+    set_dev(h);
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    memset(out, 0, sizeof *out);
+    for (size_t i = 0; i < h->prof_used; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]));
+        out->ms[h->prof_phase[i]] += ms;
+    }
+    for (int i = 0; i < DRSF_NUM_PHASES; ++i) out->launches[i] = h->prof_launch[i];
+    out->batches = h->prof_batches;
+    h->prof_on = false;
+    return DRSF_OK;
+}
+
+const char *drsf_phase_name(int phase) {
+    return phase >= 0 && phase < DRSF_NUM_PHASES ? kPhaseNames[phase] : "?";
 }
 
 void drsf_destroy(drsf_handle h) { destroy_all(h); }
