@@ -186,8 +186,8 @@ def phase_bytes(st: dict, n: int, op: int) -> dict:
         aff, det, sc, c = st["affected"], st["detached"], st["scanned"], st["candidates"]
         out["del_claim"] = 8 * b + 40 * a + 12 * st["tree_cut"]
         out["affected"] = 8 * n + 12 * aff
-        out["jump"] = 16 * aff * max(st["jump_rounds"], 1) + 16 * aff + 4 * det
-        out["scan"] = 28 * det + 8 * sc + 20 * c
+        out["jump"] = 16 * aff * max(st["jump_rounds"], 1) + 76 * aff + 4 * det
+        out["scan"] = 40 * det + 8 * sc + 32 * c
         out["active"] = 16 * aff + 16 * st["active"]
     c, ner = st["candidates"], st["replacement"]
     out["hook"] = 80 * c + 16 * ner
@@ -290,11 +290,17 @@ def run_ours(args, rank, ws, local):
     # roofline of the dominant phase (kernel), from live events + the
     # algorithmic byte model over the same K steps
     pbytes = {}
+    opbytes = {"insert": {}, "delete": {}}
     for k in range(K):
-        for op in (0, 1):
+        for op, oname in ((0, "insert"), (1, "delete")):
             for ph, by in phase_bytes(steps[W + k][op][1], g.n, op).items():
                 pbytes[ph] = pbytes.get(ph, 0) + by
-    phases = {ph: v for ph, v in prof.items() if ph != "batches"}
+                opbytes[oname][ph] = opbytes[oname].get(ph, 0) + by
+    phases = {}
+    for oname in ("insert", "delete"):
+        for ph, (ms, nl) in prof[oname].items():
+            t = phases.get(ph, (0.0, 0))
+            phases[ph] = (t[0] + ms, t[1] + nl)
     dom = max(phases, key=lambda p: phases[p][0])
     dom_ms, dom_launch = phases[dom]
     per_launch_bytes = pbytes.get(dom, 0) / max(dom_launch, 1)
@@ -309,10 +315,19 @@ def run_ours(args, rank, ws, local):
                 "algorithmic_bytes_per_launch": int(per_launch_bytes),
                 "ms_per_launch": round(per_launch_ms, 5)}
     step_total_ms = sum(v[0] for v in phases.values())
-    phase_table = {p: {"ms_per_step": round(v[0] / K, 4), "share": round(v[0] / step_total_ms, 4),
-                       "launches": int(v[1]),
-                       "GBps": round(pbytes.get(p, 0) / (v[0] / 1e3) / 1e9, 1) if v[0] > 0 else None}
-                   for p, v in phases.items() if v[1] > 0}
+    phase_table = {}
+    for oname in ("insert", "delete"):
+        phase_table[oname] = {
+            p: {"ms_per_batch": round(v[0] / K, 4), "share_of_step": round(v[0] / step_total_ms, 4),
+                "launches": int(v[1]),
+                "GBps": round(opbytes[oname].get(p, 0) / (v[0] / 1e3) / 1e9, 1) if v[0] > 0 else None}
+            for p, v in prof[oname].items() if v[1] > 0}
+    def _mean(op, key):
+        return round(float(np.mean([steps[W + k][op][1][key] for k in range(K)])), 1)
+    batch_stats = {oname: {key: _mean(op, key) for key in (
+        "applied", "tree_cut", "affected", "detached", "scanned", "candidates", "hook_rounds", "replacement",
+        "rank_rounds", "active", "reversed", "mark_rounds", "jump_rounds")} for op, oname in ((0, "insert"),
+                                                                                        (1, "delete"))}
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -359,7 +374,8 @@ def run_ours(args, rank, ws, local):
                              "p99": round(float(np.percentile(lat, 99)), 4),
                              "insert_p50": round(float(np.median(ins_ms)), 4),
                              "delete_p50": round(float(np.median(del_ms)), 4)},
-        "roofline": roofline, "phases": phase_table, "e2e": e2e, "cpu_baseline": cpu,
+        "roofline": roofline, "phases": phase_table, "batch_stats": batch_stats, "e2e": e2e,
+        "cpu_baseline": cpu,
         "gpu_launches": int(sum(v[1] for v in phases.values())),
         "clocks": clocks,
     }

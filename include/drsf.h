@@ -94,7 +94,8 @@ typedef struct {
     int64_t applied;       /* edges actually inserted / deleted */
     int64_t tree_cut;      /* deleted edges that were tree edges (delete) */
     int64_t affected;      /* vertices of trees that lost an edge (delete) */
-    int64_t detached;      /* vertices whose tree root changed after the cut */
+    int64_t detached;      /* rows scanned for cross edges: vertices of cut trees
+                              outside the heaviest piece of their tree (delete) */
     int64_t scanned;       /* adjacency entries scanned for cross edges */
     int64_t candidates;    /* cross edges found */
     int64_t hook_rounds;   /* hook-and-compress rounds */
@@ -197,9 +198,9 @@ DRSF_API drsf_status drsf_export_edges(drsf_handle h, int32_t *out, int64_t cap,
  */
 #define DRSF_NUM_PHASES 12
 typedef struct {
-    double ms[DRSF_NUM_PHASES];        /* summed device time per phase */
-    int64_t launches[DRSF_NUM_PHASES]; /* kernel launches per phase */
-    int64_t batches;                   /* batches timed */
+    double ms[2][DRSF_NUM_PHASES];        /* [op][phase] summed device time (ms) */
+    int64_t launches[2][DRSF_NUM_PHASES]; /* [op][phase] kernel launches */
+    int64_t batches[2];                   /* [op] batches timed */
 } drsf_profile_t;
 DRSF_API drsf_status drsf_profile_start(drsf_handle h, int64_t max_batches);
 DRSF_API drsf_status drsf_profile_stop(drsf_handle h, drsf_profile_t *out, drsf_stream stream);

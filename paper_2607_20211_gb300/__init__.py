@@ -57,8 +57,8 @@ NUM_PHASES = 12
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * NUM_PHASES), ("launches", ctypes.c_int64 * NUM_PHASES),
-                ("batches", ctypes.c_int64)]
+    _fields_ = [("ms", (ctypes.c_double * NUM_PHASES) * 2), ("launches", (ctypes.c_int64 * NUM_PHASES) * 2),
+                ("batches", ctypes.c_int64 * 2)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -269,13 +269,17 @@ class DynamicForest:
             raise DRSFError(st, "drsf_profile_start")
 
     def profile_stop(self) -> dict:
-        """Stop timing; {phase: (ms, launches)} plus 'batches'."""
+        """Stop timing; {"insert"|"delete": {phase: (ms, launches)}} plus
+        the number of batches of each kind under "batches"."""
         p = Profile()
         st = _lib.drsf_profile_stop(self._h, ctypes.byref(p), _stream_ptr(self._stream))
         if st:
             raise DRSFError(st, "drsf_profile_stop")
-        out = {_lib.drsf_phase_name(i).decode(): (p.ms[i], p.launches[i]) for i in range(NUM_PHASES)}
-        out["batches"] = p.batches
+        out = {}
+        for o, name in ((0, "insert"), (1, "delete")):
+            out[name] = {_lib.drsf_phase_name(i).decode(): (p.ms[o][i], p.launches[o][i])
+                         for i in range(NUM_PHASES)}
+        out["batches"] = {"insert": p.batches[0], "delete": p.batches[1]}
         return out
 
     def close(self) -> None:

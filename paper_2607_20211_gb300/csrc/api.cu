@@ -52,7 +52,10 @@ struct drsf_ctx {
     int *att_x = nullptr, *newrep = nullptr, *A = nullptr, *act = nullptr, *pold = nullptr, *D = nullptr;
     int *chx = nullptr, *chy = nullptr;
     unsigned *aff_ep = nullptr, *cut_ep = nullptr, *pstamp = nullptr, *att_ep = nullptr, *rep_ep = nullptr;
-    u64 *best0 = nullptr, *best1 = nullptr, *er = nullptr;
+    u64 *best0 = nullptr, *best1 = nullptr, *er = nullptr, *heavy = nullptr;
+    int *rold = nullptr;
+    unsigned *wgt = nullptr;
+    PairTable pt{};
     unsigned char *mark = nullptr;
     int *pdeg = nullptr, *pcur = nullptr, *poff = nullptr, *adj = nullptr, *apos = nullptr;
     int *val0 = nullptr, *val1 = nullptr, *nx0 = nullptr, *nx1 = nullptr;
@@ -78,10 +81,12 @@ struct drsf_ctx {
     // per-phase profiling
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;      // pairs per (batch, phase)
-    std::vector<int> prof_phase;           // phase of each pair
+    std::vector<int> prof_phase;           // op * DRSF_NUM_PHASES + phase of each pair
+    int prof_op = 0;
     size_t prof_used = 0;                  // pairs used
     long long prof_batches = 0;
-    long long prof_launch[DRSF_NUM_PHASES] = {0};
+    long long prof_launch[2][DRSF_NUM_PHASES] = {{0}};
+    long long prof_nb[2] = {0, 0};
 };
 
 // Phases of one batch, in launch order.
@@ -106,12 +111,12 @@ static const char *kPhaseNames[DRSF_NUM_PHASES] = {
 static void prof_begin(drsf_ctx *h, int phase, cudaStream_t s) {
     if (!h->prof_on || 2 * (h->prof_used + 1) > h->prof_ev.size()) return;
     cudaEventRecord(h->prof_ev[2 * h->prof_used], s);
-    h->prof_phase[h->prof_used] = phase;
+    h->prof_phase[h->prof_used] = h->prof_op * DRSF_NUM_PHASES + phase;
 }
 static void prof_end(drsf_ctx *h, int phase, int launches, cudaStream_t s) {
     if (!h->prof_on || 2 * (h->prof_used + 1) > h->prof_ev.size()) return;
     cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], s);
-    h->prof_launch[phase] += launches;
+    h->prof_launch[h->prof_op][phase] += launches;
     h->prof_used++;
 }
 
@@ -281,9 +286,18 @@ static drsf_status ensure_batch(drsf_ctx *h, long long len, cudaStream_t s) {
     hfree(h, &h->nkey, s);
     hfree(h, &h->nslot, s);
     hfree(h, &h->cutlist, s);
+    hfree(h, &h->pt.pk, s);
+    hfree(h, &h->pt.mk, s);
     CKA(halloc(h, &h->nkey, (size_t)cap, s));
     CKA(halloc(h, &h->nslot, (size_t)cap, s));
     CKA(halloc(h, &h->cutlist, (size_t)cap, s));
+    // pair table: room for ~8 piece pairs per batch edge at load <= 1/2
+    u64 T = pow2_at_least((u64)cap * 16);
+    CKA(halloc(h, &h->pt.pk, T, s));
+    CKA(halloc(h, &h->pt.mk, T, s));
+    CK(cudaMemsetAsync(h->pt.pk, 0xFF, T * sizeof(u64), s));
+    CK(cudaMemsetAsync(h->pt.mk, 0xFF, T * sizeof(u64), s));
+    h->pt.mask = T - 1;
     h->batch_cap = cap;
     return DRSF_OK;
 }
@@ -402,6 +416,9 @@ static drsf_status alloc_work(drsf_ctx *h, cudaStream_t s) {
     CKA(halloc(h, &h->rep_ep, n, s));
     CKA(halloc(h, &h->best0, n, s));
     CKA(halloc(h, &h->best1, n, s));
+    CKA(halloc(h, &h->heavy, n, s));
+    CKA(halloc(h, &h->rold, n, s));
+    CKA(halloc(h, &h->wgt, n, s));
     CKA(halloc(h, &h->er, n, s));
     CKA(halloc(h, &h->mark, n, s));
     CKA(halloc(h, &h->pdeg, n + 1, s));
@@ -467,7 +484,9 @@ static drsf_status create_impl(drsf_ctx *h, const int32_t *edges, int64_t m, con
     CK(cudaMemcpyAsync(h->parent, parent, (size_t)n * sizeof(int), cudaMemcpyDeviceToDevice, s));
     // representatives of F by pointer jumping over all vertices
     CK(launch_copy_parent(n, h->parent, h->J0, s));
-    CK(launch_jump(h->dev, nullptr, 0, n, h->ctl, h->J0, h->J1, h->rep, h->D, 0, s));
+    Csr g0{h->off, h->used, h->col};
+    CK(launch_jump(h->dev, nullptr, 0, n, h->ctl, h->J0, h->J1, h->rep, h->D, 0, h->rold, h->wgt, h->heavy, g0,
+                   s));
     Ctl c{};
     CK(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -546,7 +565,11 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
     if (st) return st;
     Ctl *ctl = h->ctl;
     Csr g{h->off, h->used, h->col};
-    if (h->prof_on) h->prof_batches++;
+    if (h->prof_on) {
+        h->prof_batches++;
+        h->prof_op = op;
+        h->prof_nb[op]++;
+    }
     prof_begin(h, PH_BEGIN, s);
     CK(launch_begin(ctl, op, len, s));
     CK(launch_validate_batch(batch, len, h->n, ctl, s));
@@ -567,16 +590,17 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
                             h->cutlist, s));
         prof_end(h, PH_DEL_CLAIM, len > 0 ? 1 : 0, s);
         prof_begin(h, PH_AFF, s);
-        CK(launch_aff_collect(h->dev, h->n, h->rep, h->aff_ep, h->parent, h->J0, h->A, ctl, s));
+        CK(launch_aff_collect(h->dev, h->n, h->rep, h->aff_ep, h->parent, h->J0, h->A, h->rold, ctl, s));
         prof_end(h, PH_AFF, 1, s);
         prof_begin(h, PH_JUMP, s);
-        CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->J0, h->J1, h->rep, h->D, 1, s));
+        CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->J0, h->J1, h->rep, h->D, 1, h->rold, h->wgt, h->heavy, g, s));
         prof_end(h, PH_JUMP, 1, s);
         prof_begin(h, PH_SCAN, s);
-        CK(launch_scan_rows(h->dev, h->D, ctl, g, h->rep, h->cut_ep, h->ck[0], h->ca[0], h->cb[0], h->cand_cap,
-                            s));
-        CK(launch_scan_ovf(h->dev, h->ovf, ctl, h->rep, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
-        prof_end(h, PH_SCAN, 2, s);
+        CK(launch_scan_rows(h->dev, h->D, ctl, g, h->rep, h->rold, h->heavy, h->pt, h->ck[0], h->ca[0], h->cb[0],
+                            h->cand_cap, s));
+        CK(launch_scan_ovf(h->dev, h->ovf, ctl, h->rep, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
+        CK(launch_pairs_compact(h->dev, ctl, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
+        prof_end(h, PH_SCAN, 3, s);
     }
     prof_begin(h, PH_HOOK, s);
     CK(launch_boruvka(h->dev, ctl, h->ck[0], h->ca[0], h->cb[0], h->ck[1], h->ca[1], h->cb[1], h->comp, h->best0,
@@ -770,7 +794,8 @@ drsf_status drsf_profile_start(drsf_handle h, int64_t max_batches) {
     h->prof_phase.assign(pairs, 0);
     h->prof_used = 0;
     h->prof_batches = 0;
-    for (int i = 0; i < DRSF_NUM_PHASES; ++i) h->prof_launch[i] = 0;
+    memset(h->prof_launch, 0, sizeof h->prof_launch);
+    h->prof_nb[0] = h->prof_nb[1] = 0;
     h->prof_on = true;
     return DRSF_OK;
 }
@@ -783,10 +808,13 @@ drsf_status drsf_profile_stop(drsf_handle h, drsf_profile_t *out, drsf_stream st
     for (size_t i = 0; i < h->prof_used; ++i) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]));
-        out->ms[h->prof_phase[i]] += ms;
+        int k = h->prof_phase[i];
+        out->ms[k / DRSF_NUM_PHASES][k % DRSF_NUM_PHASES] += ms;
     }
-    for (int i = 0; i < DRSF_NUM_PHASES; ++i) out->launches[i] = h->prof_launch[i];
-    out->batches = h->prof_batches;
+    for (int o = 0; o < 2; ++o) {
+        for (int i = 0; i < DRSF_NUM_PHASES; ++i) out->launches[o][i] = h->prof_launch[o][i];
+        out->batches[o] = h->prof_nb[o];
+    }
     h->prof_on = false;
     return DRSF_OK;
 }

@@ -117,6 +117,46 @@ __device__ __forceinline__ long long agg_append(u64 *ctr, bool pred) {
     return (long long)(base + __popc(m & ((1u << lane) - 1u)));
 }
 
+// Warp-level pre-reduction of a 64-bit atomicMin: lanes with the same
+// target index combine their values (minimum over the group, taken as the
+// minimum high word, then the minimum low word among lanes holding it) and
+// one lane per group issues the atomic.  Removes the hot-address contention
+// of many lanes hitting one component.
+__device__ __forceinline__ void warp_atomic_min_u64(u64 *arr, int idx, u64 k, bool pred) {
+    unsigned act = __activemask();
+    unsigned m = __ballot_sync(act, pred);
+    if (!pred) return;
+    unsigned grp = __match_any_sync(m, idx);
+    unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;
+    unsigned hmin = __reduce_min_sync(grp, hi);
+    unsigned lmin = __reduce_min_sync(grp, hi == hmin ? lo : 0xFFFFFFFFu);
+    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicMin(&arr[idx], ((u64)hmin << 32) | lmin);
+}
+
+// Pair table: piece pair (min, max) -> minimum edge key between the two
+// pieces.  Probing is bounded; a pair that finds no slot returns false and
+// the caller keeps the edge as a plain candidate instead.
+#define PAIR_PROBES 64
+__device__ __forceinline__ bool pair_min(u64 *pk, u64 *mk, u64 mask, int a, int b, u64 key) {
+    u64 pair = a < b ? ((u64)(unsigned)a << 32) | (unsigned)b : ((u64)(unsigned)b << 32) | (unsigned)a;
+    u64 s = hslot(pair, mask);
+    for (int p = 0; p < PAIR_PROBES; ++p) {
+        u64 cur = __ldcg(&pk[s]);
+        if (cur == EMPTY_KEY) {
+            u64 old = atomicCAS(&pk[s], EMPTY_KEY, pair);
+            if (old == EMPTY_KEY || old == pair) {
+                atomicMin(&mk[s], key);
+                return true;
+            }
+        } else if (cur == pair) {
+            atomicMin(&mk[s], key);
+            return true;
+        }
+        s = (s + 1) & mask;
+    }
+    return false;
+}
+
 __device__ __forceinline__ u64 globaltimer_ns() {
     u64 t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

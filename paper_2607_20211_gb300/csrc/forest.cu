@@ -43,15 +43,17 @@ __global__ void k_begin(Ctl *ctl, int op, long long len) {
 // Delete: list the vertices of every tree that lost a tree edge (its old
 // root was stamped by the cut) and seed J0 = parent (the cut forest F^).
 __global__ void k_aff_collect(int n, const int *rep, const unsigned *aff_ep, const int *parent, int *J0, int *A,
-                              Ctl *ctl) {
+                              int *rold, Ctl *ctl) {
     if (*(volatile int *)&ctl->skip) return;
     unsigned ep = ctl->epoch;
     GS_LOOP(v, n) {
-        bool in = aff_ep[rep[v]] == ep;
+        int r = rep[v];
+        bool in = aff_ep[r] == ep;
         long long p = agg_append(&ctl->naff, in);
         if (in) {
             A[p] = (int)v;
             J0[v] = parent[v];
+            rold[v] = r;
         }
     }
 }
@@ -66,7 +68,7 @@ __global__ void k_copy(int n, const int *src, int *dst) {
 // mode (1) a vertex whose new root differs from its old rep is detached and
 // listed in D.
 __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J0, int *J1, int *rep,
-                       int *D, int mode) {
+                       int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g) {
     if (*(volatile int *)&ctl->skip) return;
     long long cnt = use_list ? (long long)ctl->naff : cnt_static;
     int *Jc = J0, *Jn = J1;
@@ -91,15 +93,50 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
         int *t = Jc; Jc = Jn; Jn = t;
         if (!again) break;
     }
-    for (long long i = gtid(); i < cnt; i += gstride()) {
-        int v = use_list ? A[i] : (int)i;
-        int root = LD(Jc[v]);
-        bool det = mode == 1 && root != rep[v];
-        rep[v] = root;
-        long long p = agg_append(&ctl->ndet, det);
-        if (det) D[p] = v;
-    }
     if (gtid() == 0) ctl->jump_rounds = r + 1;
+    if (mode == 0) {
+        for (long long i = gtid(); i < cnt; i += gstride()) {
+            int v = use_list ? A[i] : (int)i;
+            rep[v] = LD(Jc[v]);
+        }
+        return;
+    }
+    // Delete: choose the rows to scan for cross edges.  Every cross edge
+    // joins two pieces of one old tree, so scanning all pieces but one per
+    // tree finds each of them; the piece left out is the heaviest (largest
+    // sum of row lengths), which keeps the scan small when a cut near the
+    // root detaches most of a tree.
+    for (long long i = gtid(); i < cnt; i += gstride()) {
+        int v = A[i];
+        int root = LD(Jc[v]);
+        rep[v] = root;
+        if (root == v) w[v] = 0;
+        if (rold[v] == v) heavy[v] = 0;
+    }
+    if (!grid_barrier(ctl)) return;
+    for (long long i = gtid(); i < cnt; i += gstride()) {
+        int v = A[i];
+        int p = LD(rep[v]);
+        long long cap = g.off[v + 1] - g.off[v];
+        long long used = g.used[v];
+        unsigned d = (unsigned)(used < cap ? used : cap) + 1u;
+        unsigned grp = __match_any_sync(__activemask(), p);
+        unsigned tot = __reduce_add_sync(grp, d);
+        if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&w[p], tot);
+    }
+    if (!grid_barrier(ctl)) return;
+    for (long long i = gtid(); i < cnt; i += gstride()) {
+        int v = A[i];
+        if (LD(rep[v]) == v) atomicMax(&heavy[rold[v]], ((u64)LD(w[v]) << 32) | (unsigned)v);
+    }
+    if (!grid_barrier(ctl)) return;
+    for (long long i = gtid(); i < cnt; i += gstride()) {
+        int v = A[i];
+        int hp = (int)(unsigned)LD(heavy[rold[v]]);
+        bool scan = LD(rep[v]) != hp;
+        long long p = agg_append(&ctl->ndet, scan);
+        if (scan) D[p] = v;
+    }
 }
 
 // Replacement edges by hook-and-compress over the trees of F^ (pieces).
@@ -147,11 +184,9 @@ __global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int 
             int a = find_root(comp, LD(ca[i]), ctl), b = find_root(comp, LD(cb[i]), ctl);
             ca[i] = a;
             cb[i] = b;
-            if (a != b) {
-                u64 k = LD(ck[i]);
-                atomicMin(&best[a], k);
-                atomicMin(&best[b], k);
-            }
+            u64 k = LD(ck[i]);
+            warp_atomic_min_u64(best, a, k, a != b);
+            warp_atomic_min_u64(best, b, k, a != b);
         }
         if (!grid_barrier(ctl)) return;
         // phase B: hook along minimum edges, keep the rest
@@ -495,8 +530,8 @@ cudaError_t launch_begin(Ctl *ctl, int op, long long len, cudaStream_t s) {
     return cudaGetLastError();
 }
 cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, const int *parent,
-                               int *J0, int *A, Ctl *ctl, cudaStream_t s) {
-    k_aff_collect<<<gsz(n), BLK, 0, s>>>(n, rep, aff_ep, parent, J0, A, ctl);
+                               int *J0, int *A, int *rold, Ctl *ctl, cudaStream_t s) {
+    k_aff_collect<<<gsz(n), BLK, 0, s>>>(n, rep, aff_ep, parent, J0, A, rold, ctl);
     (void)d;
     return cudaGetLastError();
 }
@@ -505,9 +540,11 @@ cudaError_t launch_copy_parent(int n, const int *parent, int *J0, cudaStream_t s
     return cudaGetLastError();
 }
 cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J0,
-                        int *J1, int *rep, int *D, int mode, cudaStream_t s) {
+                        int *J1, int *rep, int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g,
+                        cudaStream_t s) {
     void *args[] = {(void *)&A, (void *)&use_list, (void *)&cnt_static, (void *)&ctl, (void *)&J0,
-                    (void *)&J1, (void *)&rep, (void *)&D, (void *)&mode};
+                    (void *)&J1, (void *)&rep, (void *)&D, (void *)&mode, (void *)&rold, (void *)&w,
+                    (void *)&heavy, (void *)&g};
     return cudaLaunchCooperativeKernel((const void *)k_jump, d.coop_jump, BLK, args, 0, s);
 }
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,

@@ -310,16 +310,20 @@ __global__ void k_del_claim(const int *batch, long long len, Index ix, Csr g, u6
 }
 
 // Delete, cross-edge scan (key edges M = E(G) - E(F) - B, Algorithm 1,
-// restricted): one warp per detached vertex u (rep changed by the cut)
-// streams u's row; a live neighbour x in another piece makes the candidate
-// {u, x}.  Every cross edge has at least one detached endpoint (the trees of
-// F spanned the components of G); when both are detached the smaller id
-// emits it, so each cross edge appears once.
-__global__ void k_scan_rows(const int *D, Ctl *ctl, Csr g, const int *rep, const unsigned *cut_ep, u64 *ck,
-                            int *ca, int *cb, u64 cand_cap) {
+// restricted): one warp per listed vertex u streams u's row; a live
+// neighbour x in another piece gives the cross edge {u, x}.  The list holds
+// every vertex outside the heaviest piece H of its old tree, so each cross
+// edge has a listed endpoint; when both are listed the smaller id emits it.
+// Parallel edges between two pieces are reduced on the fly to the one with
+// the minimum key (the others can never be in the minimum spanning forest):
+// lanes of the warp with the same neighbour piece take the minimum first
+// (for a fixed u the key order is the order of x), then one lane per group
+// updates the pair table.  A pair that finds no table slot is emitted as a
+// plain candidate.
+__global__ void k_scan_rows(const int *D, Ctl *ctl, Csr g, const int *rep, const int *rold, const u64 *heavy,
+                            PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap) {
     if (*(volatile int *)&ctl->skip) return;
     long long nd = (long long)ctl->ndet;
-    unsigned ep = ctl->epoch;
     int lane = threadIdx.x & 31;
     long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -327,6 +331,7 @@ __global__ void k_scan_rows(const int *D, Ctl *ctl, Csr g, const int *rep, const
     for (long long w = warp; w < nd; w += nw) {
         int u = D[w];
         int ru = rep[u];
+        int hp = (int)(unsigned)heavy[rold[u]];
         long long o = g.off[u];
         long long cap = g.off[u + 1] - o;
         long long used = g.used[u];
@@ -340,11 +345,20 @@ __global__ void k_scan_rows(const int *D, Ctl *ctl, Csr g, const int *rep, const
                 x = __ldcs(&g.col[o + j]);
                 if (x >= 0) {
                     rx = rep[x];
-                    if (rx != ru) emit = cut_ep[rx] != ep || u < x;
+                    if (rx != ru) emit = rx == hp || u < x;
                 }
             }
-            long long p = agg_append(&ctl->ncand, emit);
+            unsigned m = __ballot_sync(0xffffffffu, emit);
+            bool raw = false;
             if (emit) {
+                unsigned grp = __match_any_sync(m, rx);
+                unsigned xmin = __reduce_min_sync(grp, (unsigned)x);
+                if (lane == __ffs(grp) - 1)
+                    raw = !pair_min(pt.pk, pt.mk, pt.mask, ru, rx, ekey((uint32_t)u, xmin));
+                if (raw) x = (int)xmin;
+            }
+            long long p = agg_append(&ctl->ncand, raw);
+            if (raw) {
                 if ((u64)p < cand_cap) {
                     ck[p] = ekey((uint32_t)u, (uint32_t)x);
                     ca[p] = ru;
@@ -358,25 +372,53 @@ __global__ void k_scan_rows(const int *D, Ctl *ctl, Csr g, const int *rep, const
     if (lane == 0 && scanned) atomicAdd((u64 *)&ctl->scanned, (u64)scanned);
 }
 
-// Delete, cross-edge scan of the overflow list (edges outside their rows).
-__global__ void k_scan_ovf(const u64 *ovf, Ctl *ctl, const int *rep, u64 *ck, int *ca, int *cb, u64 cand_cap) {
+// Delete, cross-edge scan of the overflow list (edges outside their rows),
+// through the same pair table.
+__global__ void k_scan_ovf(const u64 *ovf, Ctl *ctl, const int *rep, PairTable pt, u64 *ck, int *ca, int *cb,
+                           u64 cand_cap) {
     if (*(volatile int *)&ctl->skip) return;
     long long no = (long long)ctl->ovf_count;
     GS_LOOP(i, no) {
         u64 k = ovf[i];
-        bool emit = false;
+        bool raw = false;
         int ra = -1, rb = -1;
         if (k != TOMB_KEY) {
             ra = rep[klo(k)];
             rb = rep[khi(k)];
-            emit = ra != rb;
+            if (ra != rb) raw = !pair_min(pt.pk, pt.mk, pt.mask, ra, rb, k);
         }
-        long long p = agg_append(&ctl->ncand, emit);
-        if (emit) {
+        long long p = agg_append(&ctl->ncand, raw);
+        if (raw) {
             if ((u64)p < cand_cap) {
                 ck[p] = k;
                 ca[p] = ra;
                 cb[p] = rb;
+            } else {
+                atomicOr(&ctl->err, ERR_CAPACITY);
+            }
+        }
+    }
+}
+
+// Move the pair table into the candidate list (one candidate per piece
+// pair, its minimum key) and free the slots for the next batch.
+__global__ void k_pairs_compact(Ctl *ctl, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap) {
+    if (*(volatile int *)&ctl->skip) return;
+    GS_LOOP(i, pt.mask + 1) {
+        u64 pair = pt.pk[i];
+        bool on = pair != EMPTY_KEY;
+        u64 k = 0;
+        if (on) {
+            k = pt.mk[i];
+            pt.pk[i] = EMPTY_KEY;
+            pt.mk[i] = EMPTY_KEY;
+        }
+        long long p = agg_append(&ctl->ncand, on);
+        if (on) {
+            if ((u64)p < cand_cap) {
+                ck[p] = k;
+                ca[p] = (int)(pair >> 32);
+                cb[p] = (int)(pair & 0xFFFFFFFFu);
             } else {
                 atomicOr(&ctl->err, ERR_CAPACITY);
             }
@@ -500,14 +542,20 @@ cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u
     k_del_claim<<<gsz(len), BLK, 0, s>>>(batch, len, ix, g, ovf, parent, rep, ctl, aff_ep, cut_ep, cutlist);
     return cudaGetLastError();
 }
-cudaError_t launch_scan_rows(const Dev &d, const int *D, Ctl *ctl, Csr g, const int *rep,
-                             const unsigned *cut_ep, u64 *ck, int *ca, int *cb, u64 cand_cap, cudaStream_t s) {
-    k_scan_rows<<<d.grid, BLK, 0, s>>>(D, ctl, g, rep, cut_ep, ck, ca, cb, cand_cap);
+cudaError_t launch_scan_rows(const Dev &d, const int *D, Ctl *ctl, Csr g, const int *rep, const int *rold,
+                             const u64 *heavy, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap,
+                             cudaStream_t s) {
+    k_scan_rows<<<d.grid, BLK, 0, s>>>(D, ctl, g, rep, rold, heavy, pt, ck, ca, cb, cand_cap);
     return cudaGetLastError();
 }
-cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, u64 *ck, int *ca, int *cb,
-                            u64 cand_cap, cudaStream_t s) {
-    k_scan_ovf<<<d.nsm * 2, BLK, 0, s>>>(ovf, ctl, rep, ck, ca, cb, cand_cap);
+cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, PairTable pt, u64 *ck, int *ca,
+                            int *cb, u64 cand_cap, cudaStream_t s) {
+    k_scan_ovf<<<d.nsm * 2, BLK, 0, s>>>(ovf, ctl, rep, pt, ck, ca, cb, cand_cap);
+    return cudaGetLastError();
+}
+cudaError_t launch_pairs_compact(const Dev &d, Ctl *ctl, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap,
+                                 cudaStream_t s) {
+    k_pairs_compact<<<gsz((long long)pt.mask + 1), BLK, 0, s>>>(ctl, pt, ck, ca, cb, cand_cap);
     return cudaGetLastError();
 }
 cudaError_t launch_extract(const Dev &d, int n, Csr g, const u64 *ovf, u64 novf_max, Ctl *ctl, int *out,

@@ -33,10 +33,18 @@ cudaError_t launch_ins_place(const Dev &d, const u64 *nkey, const u64 *nslot, Ct
 cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u64 *ovf, int *parent,
                              const int *rep, Ctl *ctl, unsigned *aff_ep, unsigned *cut_ep, int *cutlist,
                              cudaStream_t s);
-cudaError_t launch_scan_rows(const Dev &d, const int *D, Ctl *ctl, Csr g, const int *rep,
-                             const unsigned *cut_ep, u64 *ck, int *ca, int *cb, u64 cand_cap, cudaStream_t s);
-cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, u64 *ck, int *ca, int *cb,
-                            u64 cand_cap, cudaStream_t s);
+struct PairTable {
+    u64 *pk;   // piece pair key, EMPTY_KEY when free
+    u64 *mk;   // minimum edge key of the pair
+    u64 mask;
+};
+cudaError_t launch_scan_rows(const Dev &d, const int *D, Ctl *ctl, Csr g, const int *rep, const int *rold,
+                             const u64 *heavy, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap,
+                             cudaStream_t s);
+cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, PairTable pt, u64 *ck, int *ca,
+                            int *cb, u64 cand_cap, cudaStream_t s);
+cudaError_t launch_pairs_compact(const Dev &d, Ctl *ctl, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap,
+                                 cudaStream_t s);
 cudaError_t launch_extract(const Dev &d, int n, Csr g, const u64 *ovf, u64 novf_max, Ctl *ctl, int *out,
                            long long cap, u64 *cnt, cudaStream_t s);
 cudaError_t launch_check_tree_edges(int n, const int *parent, Index ix, int *bad, cudaStream_t s);
@@ -45,10 +53,11 @@ cudaError_t launch_check_cross(const int *pairs, long long m, const int *rep, in
 // forest.cu ------------------------------------------------------------
 cudaError_t launch_begin(Ctl *ctl, int op, long long len, cudaStream_t s);
 cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, const int *parent,
-                               int *J0, int *A, Ctl *ctl, cudaStream_t s);
+                               int *J0, int *A, int *rold, Ctl *ctl, cudaStream_t s);
 cudaError_t launch_copy_parent(int n, const int *parent, int *J0, cudaStream_t s);
 cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J0,
-                        int *J1, int *rep, int *D, int mode, cudaStream_t s);
+                        int *J1, int *rep, int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g,
+                        cudaStream_t s);
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
                            int *comp, u64 *best0, u64 *best1, u64 *er, long long er_cap, cudaStream_t s);
 struct OrientArgs {
