@@ -53,7 +53,8 @@ struct drsf_ctx {
     int *chx = nullptr, *chy = nullptr;
     unsigned *aff_ep = nullptr, *cut_ep = nullptr, *pstamp = nullptr, *att_ep = nullptr, *rep_ep = nullptr;
     u64 *best0 = nullptr, *best1 = nullptr, *er = nullptr, *heavy = nullptr;
-    int *rold = nullptr;
+    int *rold = nullptr, *longrows = nullptr, *cdeg = nullptr;
+    unsigned char *lf = nullptr;
     unsigned *wgt = nullptr;
     PairTable pt{};
     unsigned char *mark = nullptr;
@@ -418,6 +419,9 @@ static drsf_status alloc_work(drsf_ctx *h, cudaStream_t s) {
     CKA(halloc(h, &h->best1, n, s));
     CKA(halloc(h, &h->heavy, n, s));
     CKA(halloc(h, &h->rold, n, s));
+    CKA(halloc(h, &h->longrows, n, s));
+    CKA(halloc(h, &h->cdeg, n + 1, s));
+    CKA(halloc(h, &h->lf, n + 1, s));
     CKA(halloc(h, &h->wgt, n, s));
     CKA(halloc(h, &h->er, n, s));
     CKA(halloc(h, &h->mark, n, s));
@@ -597,10 +601,10 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
         prof_end(h, PH_JUMP, 1, s);
         prof_begin(h, PH_SCAN, s);
         CK(launch_scan_rows(h->dev, h->D, ctl, g, h->rep, h->rold, h->heavy, h->pt, h->ck[0], h->ca[0], h->cb[0],
-                            h->cand_cap, s));
+                            h->cand_cap, h->longrows, s));
         CK(launch_scan_ovf(h->dev, h->ovf, ctl, h->rep, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
         CK(launch_pairs_compact(h->dev, ctl, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
-        prof_end(h, PH_SCAN, 3, s);
+        prof_end(h, PH_SCAN, 4, s);
     }
     prof_begin(h, PH_HOOK, s);
     CK(launch_boruvka(h->dev, ctl, h->ck[0], h->ca[0], h->cb[0], h->ck[1], h->ca[1], h->cb[1], h->comp, h->best0,
@@ -630,6 +634,8 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
     oa.rep_ep = h->rep_ep;
     oa.att_x = h->att_x;
     oa.newrep = h->newrep;
+    oa.lf = h->lf;
+    oa.cdeg = h->cdeg;
     prof_begin(h, PH_ORIENT, s);
     CK(launch_orient(h->dev, ctl, oa, s));
     prof_end(h, PH_ORIENT, 1, s);

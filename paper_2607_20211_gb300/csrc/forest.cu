@@ -31,6 +31,7 @@ __global__ void k_begin(Ctl *ctl, int op, long long len) {
     ctl->skip = 0;
     ctl->op = op;
     ctl->nb = ctl->ncut = ctl->naff = ctl->ndet = ctl->ncand = ctl->ner = ctl->npc = ctl->nact = 0;
+    ctl->nlong = 0;
     ctl->scanned = ctl->self_loops = ctl->dropped = ctl->tree_cut = 0;
     ctl->hook_rounds = ctl->rank_rounds = ctl->mark_rounds = ctl->jump_rounds = ctl->reversed = 0;
     ctl->batch_len = len;
@@ -253,13 +254,16 @@ __device__ int block_excl_scan(int v, int *total) {
 }
 
 // Orientation of E_r (Algorithm 2, phase 2).  The replacement edges form a
-// forest over the pieces (the super-forest).  Each super-tree is rooted at
-// its piece with the smallest root id: build the Euler circuit of each
-// super-tree from the circular adjacency lists (successor of arc a->b is the
-// arc after b->a in b's list), open it at the root, rank the arcs by
-// Wyllie's pointer jumping, and orient each edge from the arc that comes
-// first.  The child piece P of edge {x, y} (x in P) gets the oriented
-// replacement edge x -> y; every piece of the super-tree gets the new root.
+// forest over the pieces (the super-forest); each super-tree is rooted at
+// its piece with the smallest root id.  A non-root piece with a single
+// replacement edge is a leaf: its parent is its only neighbour, no tour
+// needed.  The rest (the core, a tree per super-tree that still holds the
+// root) is rooted by the Euler tour technique: circular adjacency lists give
+// the successor of arc a->b as the arc after b->a in b's list; the circuit is
+// opened at the root, the arcs are ranked by Wyllie's pointer jumping, and
+// each edge is oriented by its arc that comes first.  The child piece P of
+// edge {x, y} (x in P) gets the oriented replacement edge x -> y; every piece
+// of the super-tree gets the root as its new representative.
 __global__ void k_orient(Ctl *ctl, OrientArgs a) {
     if (*(volatile int *)&ctl->skip) return;
     const long long ner = (long long)ctl->ner;
@@ -275,6 +279,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
             a.pidx[p] = (int)id;
             a.plist[id] = p;
             a.pdeg[id] = 0;
+            a.cdeg[id] = 0;
             a.pcur[id] = 0;
         }
     }
@@ -287,13 +292,28 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         atomicAdd(&a.pdeg[LD(a.pidx[p])], 1);
     }
     if (!grid_barrier(ctl)) return;
-    // phase 3: exclusive scan of degrees -> adjacency offsets
+    // phase 2b: leaf edges; core degrees
+    for (long long i = gtid(); i < ner; i += gstride()) {
+        u64 k = a.er[i];
+        int p0 = a.rep[klo(k)], p1 = a.rep[khi(k)];
+        int id0 = LD(a.pidx[p0]), id1 = LD(a.pidx[p1]);
+        bool leaf0 = LD(a.pdeg[id0]) == 1 && LD(a.minp[find_root(a.comp, p0, ctl)]) != p0;
+        bool leaf1 = LD(a.pdeg[id1]) == 1 && LD(a.minp[find_root(a.comp, p1, ctl)]) != p1;
+        unsigned char lf = leaf0 ? 1 : (leaf1 ? 2 : 0);
+        a.lf[i] = lf;
+        if (!lf) {
+            atomicAdd(&a.cdeg[id0], 1);
+            atomicAdd(&a.cdeg[id1], 1);
+        }
+    }
+    if (!grid_barrier(ctl)) return;
+    // phase 3: exclusive scan of core degrees -> adjacency offsets
     const long long np = (long long)*(volatile u64 *)&ctl->npc;
     const long long chunk = (np + gridDim.x - 1) / gridDim.x;
     const long long lo = (long long)blockIdx.x * chunk, hi = lo + chunk < np ? lo + chunk : np;
     {
         int s = 0;
-        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) s += LD(a.pdeg[i]);
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) s += LD(a.cdeg[i]);
         int tot;
         block_excl_scan(s, &tot);
         if (threadIdx.x == 0) a.bsum[blockIdx.x] = tot;
@@ -318,7 +338,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         int carry = (int)LD(a.bsum[blockIdx.x]);
         for (long long t0 = lo; t0 < hi; t0 += blockDim.x) {
             long long i = t0 + threadIdx.x;
-            int d = i < hi ? LD(a.pdeg[i]) : 0;
+            int d = i < hi ? LD(a.cdeg[i]) : 0;
             int tot;
             int pre = block_excl_scan(d, &tot);
             if (i < hi) a.poff[i] = carry + pre;
@@ -326,8 +346,9 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         }
     }
     if (!grid_barrier(ctl)) return;
-    // phase 4: place arcs; arc 2i = (lo-piece -> hi-piece), arc 2i+1 its twin
+    // phase 4: place core arcs; arc 2i = (lo-piece -> hi-piece), 2i+1 its twin
     for (long long i = gtid(); i < 2 * ner; i += gstride()) {
+        if (LD(a.lf[i >> 1])) continue;
         u64 k = a.er[i >> 1];
         int p = a.rep[(i & 1) ? khi(k) : klo(k)];
         int id = LD(a.pidx[p]);
@@ -336,13 +357,14 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         a.apos[i] = slot;
     }
     if (!grid_barrier(ctl)) return;
-    // phase 5: Euler successors; open the circuit at each super-root
+    // phase 5: Euler successors of core arcs; open the circuit at each root
     for (long long i = gtid(); i < 2 * ner; i += gstride()) {
+        if (LD(a.lf[i >> 1])) continue;
         long long tw = i ^ 1;
         u64 k = a.er[i >> 1];
         int head = a.rep[(i & 1) ? klo(k) : khi(k)];     // source of the twin
         int id = LD(a.pidx[head]);
-        int start = LD(a.poff[id]), end = start + LD(a.pdeg[id]);
+        int start = LD(a.poff[id]), end = start + LD(a.cdeg[id]);
         int nx = LD(a.apos[tw]) + 1;
         int succ;
         if (nx == end) {
@@ -366,6 +388,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         if (gtid() == 0) ctl->flag[(r + 1) % 3] = 0;
         bool ch = false;
         for (long long i = gtid(); i < 2 * ner; i += gstride()) {
+            if (LD(a.lf[i >> 1])) continue;
             int s = LD(nc[i]);
             if (s != NIL) {
                 vn[i] = LD(vc[i]) + LD(vc[s]);
@@ -388,7 +411,10 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         u64 k = a.er[i];
         int x0 = (int)klo(k), x1 = (int)khi(k);
         int p0 = a.rep[x0], p1 = a.rep[x1];
-        bool down = LD(vc[2 * i]) > LD(vc[2 * i + 1]);   // arc p0 -> p1 first: p0 is the parent
+        unsigned char lf = LD(a.lf[i]);
+        bool down;                                 // true: p0 is the parent of p1
+        if (lf) down = lf == 2;
+        else down = LD(vc[2 * i]) > LD(vc[2 * i + 1]);
         int child = down ? p1 : p0;
         int x = down ? x1 : x0, y = down ? x0 : x1;
         a.chx[i] = x;

@@ -320,8 +320,46 @@ __global__ void k_del_claim(const int *batch, long long len, Index ix, Csr g, u6
 // (for a fixed u the key order is the order of x), then one lane per group
 // updates the pair table.  A pair that finds no table slot is emitted as a
 // plain candidate.
+// One warp-wide step of the scan: 32 consecutive entries of row u.
+__device__ __forceinline__ void scan_chunk(int u, int ru, int hp, long long o, long long j, long long used,
+                                           const Csr &g, const int *rep, PairTable pt, Ctl *ctl, u64 *ck,
+                                           int *ca, int *cb, u64 cand_cap) {
+    int lane = threadIdx.x & 31;
+    bool emit = false;
+    int x = -1, rx = -1;
+    if (j < used) {
+        x = __ldcs(&g.col[o + j]);
+        if (x >= 0) {
+            rx = rep[x];
+            if (rx != ru) emit = rx == hp || u < x;
+        }
+    }
+    unsigned m = __ballot_sync(0xffffffffu, emit);
+    bool raw = false;
+    if (emit) {
+        unsigned grp = __match_any_sync(m, rx);
+        unsigned xmin = __reduce_min_sync(grp, (unsigned)x);
+        if (lane == __ffs(grp) - 1) raw = !pair_min(pt.pk, pt.mk, pt.mask, ru, rx, ekey((uint32_t)u, xmin));
+        if (raw) x = (int)xmin;
+    }
+    long long p = agg_append(&ctl->ncand, raw);
+    if (raw) {
+        if ((u64)p < cand_cap) {
+            ck[p] = ekey((uint32_t)u, (uint32_t)x);
+            ca[p] = ru;
+            cb[p] = rx;
+        } else {
+            atomicOr(&ctl->err, ERR_CAPACITY);
+        }
+    }
+}
+
+// Rows longer than this are left to k_scan_long, which spreads one row over
+// the whole grid (a single warp on a hub row would serialise the batch).
+#define SCAN_LONG_ROW 2048
+
 __global__ void k_scan_rows(const int *D, Ctl *ctl, Csr g, const int *rep, const int *rold, const u64 *heavy,
-                            PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap) {
+                            PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap, int *longrows) {
     if (*(volatile int *)&ctl->skip) return;
     long long nd = (long long)ctl->ndet;
     int lane = threadIdx.x & 31;
@@ -330,46 +368,42 @@ __global__ void k_scan_rows(const int *D, Ctl *ctl, Csr g, const int *rep, const
     long long scanned = 0;
     for (long long w = warp; w < nd; w += nw) {
         int u = D[w];
-        int ru = rep[u];
-        int hp = (int)(unsigned)heavy[rold[u]];
         long long o = g.off[u];
         long long cap = g.off[u + 1] - o;
         long long used = g.used[u];
         if (used > cap) used = cap;
         scanned += used;
-        for (long long j0 = 0; j0 < used; j0 += 32) {
-            long long j = j0 + lane;
-            bool emit = false;
-            int x = -1, rx = -1;
-            if (j < used) {
-                x = __ldcs(&g.col[o + j]);
-                if (x >= 0) {
-                    rx = rep[x];
-                    if (rx != ru) emit = rx == hp || u < x;
-                }
-            }
-            unsigned m = __ballot_sync(0xffffffffu, emit);
-            bool raw = false;
-            if (emit) {
-                unsigned grp = __match_any_sync(m, rx);
-                unsigned xmin = __reduce_min_sync(grp, (unsigned)x);
-                if (lane == __ffs(grp) - 1)
-                    raw = !pair_min(pt.pk, pt.mk, pt.mask, ru, rx, ekey((uint32_t)u, xmin));
-                if (raw) x = (int)xmin;
-            }
-            long long p = agg_append(&ctl->ncand, raw);
-            if (raw) {
-                if ((u64)p < cand_cap) {
-                    ck[p] = ekey((uint32_t)u, (uint32_t)x);
-                    ca[p] = ru;
-                    cb[p] = rx;
-                } else {
-                    atomicOr(&ctl->err, ERR_CAPACITY);
-                }
-            }
+        if (used > SCAN_LONG_ROW) {
+            if (lane == 0) longrows[atomicAdd(&ctl->nlong, 1ull)] = u;
+            continue;
         }
+        int ru = rep[u];
+        int hp = (int)(unsigned)heavy[rold[u]];
+        for (long long j0 = 0; j0 < used; j0 += 32)
+            scan_chunk(u, ru, hp, o, j0 + lane, used, g, rep, pt, ctl, ck, ca, cb, cand_cap);
     }
     if (lane == 0 && scanned) atomicAdd((u64 *)&ctl->scanned, (u64)scanned);
+}
+
+// The long rows, each split over all warps of the grid.
+__global__ void k_scan_long(Ctl *ctl, Csr g, const int *rep, const int *rold, const u64 *heavy, PairTable pt,
+                            u64 *ck, int *ca, int *cb, u64 cand_cap, const int *longrows) {
+    if (*(volatile int *)&ctl->skip) return;
+    long long nl = (long long)ctl->nlong;
+    int lane = threadIdx.x & 31;
+    long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long h = 0; h < nl; ++h) {
+        int u = longrows[h];
+        long long o = g.off[u];
+        long long cap = g.off[u + 1] - o;
+        long long used = g.used[u];
+        if (used > cap) used = cap;
+        int ru = rep[u];
+        int hp = (int)(unsigned)heavy[rold[u]];
+        for (long long j0 = warp * 32; j0 < used; j0 += nw * 32)
+            scan_chunk(u, ru, hp, o, j0 + lane, used, g, rep, pt, ctl, ck, ca, cb, cand_cap);
+    }
 }
 
 // Delete, cross-edge scan of the overflow list (edges outside their rows),
@@ -544,8 +578,9 @@ cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u
 }
 cudaError_t launch_scan_rows(const Dev &d, const int *D, Ctl *ctl, Csr g, const int *rep, const int *rold,
                              const u64 *heavy, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap,
-                             cudaStream_t s) {
-    k_scan_rows<<<d.grid, BLK, 0, s>>>(D, ctl, g, rep, rold, heavy, pt, ck, ca, cb, cand_cap);
+                             int *longrows, cudaStream_t s) {
+    k_scan_rows<<<d.grid, BLK, 0, s>>>(D, ctl, g, rep, rold, heavy, pt, ck, ca, cb, cand_cap, longrows);
+    k_scan_long<<<d.grid, BLK, 0, s>>>(ctl, g, rep, rold, heavy, pt, ck, ca, cb, cand_cap, longrows);
     return cudaGetLastError();
 }
 cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, PairTable pt, u64 *ck, int *ca,

@@ -40,7 +40,7 @@ struct PairTable {
 };
 cudaError_t launch_scan_rows(const Dev &d, const int *D, Ctl *ctl, Csr g, const int *rep, const int *rold,
                              const u64 *heavy, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap,
-                             cudaStream_t s);
+                             int *longrows, cudaStream_t s);
 cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, PairTable pt, u64 *ck, int *ca,
                             int *cb, u64 cand_cap, cudaStream_t s);
 cudaError_t launch_pairs_compact(const Dev &d, Ctl *ctl, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap,
@@ -71,6 +71,8 @@ struct OrientArgs {
     int *chx, *chy;
     unsigned *att_ep, *rep_ep;
     int *att_x, *newrep;
+    unsigned char *lf;   // per replacement edge: 0 core, 1 lo-side piece is a leaf, 2 hi-side
+    int *cdeg;           // core degree per dense piece
 };
 cudaError_t launch_orient(const Dev &d, Ctl *ctl, OrientArgs a, cudaStream_t s);
 cudaError_t launch_active(const Dev &d, const int *L, int use_list, long long cnt_static, Ctl *ctl, int *rep,
