@@ -53,7 +53,8 @@ struct drsf_ctx {
     int *chx = nullptr, *chy = nullptr;
     unsigned *aff_ep = nullptr, *cut_ep = nullptr, *pstamp = nullptr, *att_ep = nullptr, *rep_ep = nullptr;
     u64 *best0 = nullptr, *best1 = nullptr, *er = nullptr, *heavy = nullptr;
-    int *rold = nullptr, *longrows = nullptr, *cdeg = nullptr;
+    int *rold = nullptr, *cdeg = nullptr;
+    long long *roff = nullptr;
     unsigned char *lf = nullptr;
     unsigned *wgt = nullptr;
     PairTable pt{};
@@ -419,7 +420,7 @@ static drsf_status alloc_work(drsf_ctx *h, cudaStream_t s) {
     CKA(halloc(h, &h->best1, n, s));
     CKA(halloc(h, &h->heavy, n, s));
     CKA(halloc(h, &h->rold, n, s));
-    CKA(halloc(h, &h->longrows, n, s));
+    CKA(halloc(h, &h->roff, n + 1, s));
     CKA(halloc(h, &h->cdeg, n + 1, s));
     CKA(halloc(h, &h->lf, n + 1, s));
     CKA(halloc(h, &h->wgt, n, s));
@@ -489,8 +490,8 @@ static drsf_status create_impl(drsf_ctx *h, const int32_t *edges, int64_t m, con
     // representatives of F by pointer jumping over all vertices
     CK(launch_copy_parent(n, h->parent, h->J0, s));
     Csr g0{h->off, h->used, h->col};
-    CK(launch_jump(h->dev, nullptr, 0, n, h->ctl, h->J0, h->J1, h->rep, h->D, 0, h->rold, h->wgt, h->heavy, g0,
-                   s));
+    CK(launch_jump(h->dev, nullptr, 0, n, h->ctl, h->J0, h->rep, h->D, 0, h->rold, h->wgt, h->heavy, g0, h->roff,
+                   h->bsum, s));
     Ctl c{};
     CK(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -597,14 +598,15 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
         CK(launch_aff_collect(h->dev, h->n, h->rep, h->aff_ep, h->parent, h->J0, h->A, h->rold, ctl, s));
         prof_end(h, PH_AFF, 1, s);
         prof_begin(h, PH_JUMP, s);
-        CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->J0, h->J1, h->rep, h->D, 1, h->rold, h->wgt, h->heavy, g, s));
+        CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->J0, h->rep, h->D, 1, h->rold, h->wgt, h->heavy, g, h->roff,
+                       h->bsum, s));
         prof_end(h, PH_JUMP, 1, s);
         prof_begin(h, PH_SCAN, s);
-        CK(launch_scan_rows(h->dev, h->D, ctl, g, h->rep, h->rold, h->heavy, h->pt, h->ck[0], h->ca[0], h->cb[0],
-                            h->cand_cap, h->longrows, s));
+        CK(launch_scan_rows(h->dev, h->D, h->roff, ctl, g, h->rep, h->rold, h->heavy, h->pt, h->ck[0], h->ca[0],
+                            h->cb[0], h->cand_cap, s));
         CK(launch_scan_ovf(h->dev, h->ovf, ctl, h->rep, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
         CK(launch_pairs_compact(h->dev, ctl, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
-        prof_end(h, PH_SCAN, 4, s);
+        prof_end(h, PH_SCAN, 3, s);
     }
     prof_begin(h, PH_HOOK, s);
     CK(launch_boruvka(h->dev, ctl, h->ck[0], h->ca[0], h->cb[0], h->ck[1], h->ca[1], h->cb[1], h->comp, h->best0,

@@ -55,7 +55,6 @@ struct Ctl {
     u64 ner;                // replacement edges
     u64 npc;                // distinct pieces touched by E_r
     u64 nact;               // active vertices (path reversal)
-    u64 nlong;              // long rows left to the grid-wide scan
     u64 ovf_count;          // overflow list length (grows until rebuild)
     long long edges;        // live undirected edges of G
     long long htomb;        // index tombstones
@@ -156,6 +155,67 @@ __device__ __forceinline__ bool pair_min(u64 *pk, u64 *mk, u64 mask, int a, int 
         s = (s + 1) & mask;
     }
     return false;
+}
+
+// Block-aggregated append: one atomicAdd per block.  Every thread of the
+// block must call it (the loop around it must be block-uniform); the slots
+// of a block are contiguous and ordered by thread index.
+__device__ __forceinline__ long long block_append(u64 *ctr, bool pred) {
+    __shared__ unsigned s_w[32];
+    __shared__ u64 s_base;
+    unsigned m = __ballot_sync(0xffffffffu, pred);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) s_w[w] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0;
+        int nw = (blockDim.x + 31) >> 5;
+        for (int k = 0; k < nw; ++k) {
+            unsigned c = s_w[k];
+            s_w[k] = tot;
+            tot += c;
+        }
+        s_base = tot ? atomicAdd(ctr, (u64)tot) : 0;
+    }
+    __syncthreads();
+    long long r = pred ? (long long)(s_base + s_w[w] + __popc(m & ((1u << lane) - 1u))) : -1;
+    __syncthreads();
+    return r;
+}
+
+// Block-wide exclusive scan (any blockDim multiple of 32, <= 1024);
+// *total receives the block sum.  All threads must call it.
+__device__ __forceinline__ long long block_excl_scan_ll(long long v, long long *total) {
+    __shared__ long long s_ws[32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        long long t = lane < nw ? s_ws[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) s_ws[lane] = t;
+    }
+    __syncthreads();
+    long long pre = (w > 0 ? s_ws[w - 1] : 0) + x - v;
+    *total = s_ws[nw - 1];
+    __syncthreads();
+    return pre;
+}
+
+// 64-bit minimum over a group of lanes (mask from __match_any_sync).
+__device__ __forceinline__ u64 group_min_u64(unsigned grp, u64 k) {
+    unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;
+    unsigned hmin = __reduce_min_sync(grp, hi);
+    unsigned lmin = __reduce_min_sync(grp, hi == hmin ? lo : 0xFFFFFFFFu);
+    return ((u64)hmin << 32) | lmin;
 }
 
 __device__ __forceinline__ u64 globaltimer_ns() {

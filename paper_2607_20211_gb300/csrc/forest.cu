@@ -31,7 +31,6 @@ __global__ void k_begin(Ctl *ctl, int op, long long len) {
     ctl->skip = 0;
     ctl->op = op;
     ctl->nb = ctl->ncut = ctl->naff = ctl->ndet = ctl->ncand = ctl->ner = ctl->npc = ctl->nact = 0;
-    ctl->nlong = 0;
     ctl->scanned = ctl->self_loops = ctl->dropped = ctl->tree_cut = 0;
     ctl->hook_rounds = ctl->rank_rounds = ctl->mark_rounds = ctl->jump_rounds = ctl->reversed = 0;
     ctl->batch_len = len;
@@ -47,10 +46,11 @@ __global__ void k_aff_collect(int n, const int *rep, const unsigned *aff_ep, con
                               int *rold, Ctl *ctl) {
     if (*(volatile int *)&ctl->skip) return;
     unsigned ep = ctl->epoch;
-    GS_LOOP(v, n) {
-        int r = rep[v];
-        bool in = aff_ep[r] == ep;
-        long long p = agg_append(&ctl->naff, in);
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
+        long long v = base + threadIdx.x;
+        int r = v < n ? rep[v] : 0;
+        bool in = v < n && aff_ep[r] == ep;
+        long long p = block_append(&ctl->naff, in);
         if (in) {
             A[p] = (int)v;
             J0[v] = parent[v];
@@ -63,57 +63,48 @@ __global__ void k_copy(int n, const int *src, int *dst) {
     GS_LOOP(v, n) dst[v] = src[v];
 }
 
-// Representatives (Algorithm 1, parallel pointer jumping): J <- J o J over
-// the listed vertices until no pointer moves; then rep[v] = J[v].  Ping-pong
-// buffers keep every round a pure function of the previous one.  In delete
-// mode (1) a vertex whose new root differs from its old rep is detached and
-// listed in D.
-__global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J0, int *J1, int *rep,
-                       int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g) {
+// Root of v in the forest J by pointer jumping with path halving, in place:
+// every J[x] only ever moves to an ancestor of x, so concurrent walks over
+// shared paths stay correct and shorten each other's paths (no round
+// barrier is needed).  The walk is bounded; a cycle latches ERR_ROUNDS.
+__device__ __forceinline__ int find_halving(int *J, int v, Ctl *ctl) {
+    int x = v;
+    for (int it = 0; it < (1 << 22); ++it) {
+        int p = __ldcg(&J[x]);
+        int gp = __ldcg(&J[p]);
+        if (p == gp) return p;
+        J[x] = gp;
+        x = gp;
+    }
+    atomicOr(&ctl->err, ERR_ROUNDS);
+    return x;
+}
+
+// Representatives (Algorithm 1, parallel pointer jumping) of the listed
+// vertices: rep[v] = root of v in F^ (J starts as a copy of parent).
+// Delete mode (1) then chooses the rows to scan for cross edges: every cross
+// edge joins two pieces of one old tree, so scanning all pieces but one per
+// tree finds each of them; the piece left out is the heaviest (largest sum
+// of row lengths), which keeps the scan small when a cut near the root
+// detaches most of a tree.  The listed rows D get an exclusive prefix sum of
+// their lengths in roff (roff[ndet] = total) for the load-balanced scan.
+__global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *rep, int *D,
+                       int mode, const int *rold, unsigned *w, u64 *heavy, Csr g, long long *roff,
+                       long long *bsum) {
     if (*(volatile int *)&ctl->skip) return;
     long long cnt = use_list ? (long long)ctl->naff : cnt_static;
-    int *Jc = J0, *Jn = J1;
-    int r = 0;
-    for (;; ++r) {
-        if (r >= MAX_ROUNDS) {
-            if (gtid() == 0) atomicOr(&ctl->err, ERR_ROUNDS);
-            return;
-        }
-        if (gtid() == 0) ctl->flag[(r + 1) % 3] = 0;
-        bool ch = false;
-        for (long long i = gtid(); i < cnt; i += gstride()) {
-            int v = use_list ? A[i] : (int)i;
-            int w = LD(Jc[v]);
-            int w2 = LD(Jc[w]);
-            Jn[v] = w2;
-            ch |= (w2 != w);
-        }
-        if (__syncthreads_or(ch) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
-        if (!grid_barrier(ctl)) return;
-        int again = *(volatile int *)&ctl->flag[r % 3];
-        int *t = Jc; Jc = Jn; Jn = t;
-        if (!again) break;
-    }
-    if (gtid() == 0) ctl->jump_rounds = r + 1;
-    if (mode == 0) {
-        for (long long i = gtid(); i < cnt; i += gstride()) {
-            int v = use_list ? A[i] : (int)i;
-            rep[v] = LD(Jc[v]);
-        }
-        return;
-    }
-    // Delete: choose the rows to scan for cross edges.  Every cross edge
-    // joins two pieces of one old tree, so scanning all pieces but one per
-    // tree finds each of them; the piece left out is the heaviest (largest
-    // sum of row lengths), which keeps the scan small when a cut near the
-    // root detaches most of a tree.
     for (long long i = gtid(); i < cnt; i += gstride()) {
-        int v = A[i];
-        int root = LD(Jc[v]);
+        int v = use_list ? A[i] : (int)i;
+        int root = find_halving(J, v, ctl);
+        J[v] = root;
         rep[v] = root;
-        if (root == v) w[v] = 0;
-        if (rold[v] == v) heavy[v] = 0;
+        if (mode == 1) {
+            if (root == v) w[v] = 0;
+            if (rold[v] == v) heavy[v] = 0;
+        }
     }
+    if (gtid() == 0) ctl->jump_rounds = 1;
+    if (mode == 0) return;
     if (!grid_barrier(ctl)) return;
     for (long long i = gtid(); i < cnt; i += gstride()) {
         int v = A[i];
@@ -131,12 +122,65 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
         if (LD(rep[v]) == v) atomicMax(&heavy[rold[v]], ((u64)LD(w[v]) << 32) | (unsigned)v);
     }
     if (!grid_barrier(ctl)) return;
-    for (long long i = gtid(); i < cnt; i += gstride()) {
-        int v = A[i];
-        int hp = (int)(unsigned)LD(heavy[rold[v]]);
-        bool scan = LD(rep[v]) != hp;
-        long long p = agg_append(&ctl->ndet, scan);
-        if (scan) D[p] = v;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += gstride()) {
+        long long i = base + threadIdx.x;
+        bool scan = false;
+        int v = 0;
+        long long len = 0;
+        if (i < cnt) {
+            v = A[i];
+            int hp = (int)(unsigned)LD(heavy[rold[v]]);
+            long long cap = g.off[v + 1] - g.off[v];
+            long long used = g.used[v];
+            len = used < cap ? used : cap;
+            scan = LD(rep[v]) != hp && len > 0;
+        }
+        long long p = block_append(&ctl->ndet, scan);
+        if (scan) {
+            D[p] = v;
+            roff[p] = len;
+        }
+    }
+    if (!grid_barrier(ctl)) return;
+    // exclusive scan of roff[0..nd) in place: chunk sums, scan of the sums,
+    // chunk rescans
+    const long long nd = (long long)*(volatile u64 *)&ctl->ndet;
+    const long long chunk = (nd + gridDim.x - 1) / gridDim.x;
+    const long long lo = (long long)blockIdx.x * chunk, hi = lo + chunk < nd ? lo + chunk : nd;
+    {
+        long long sacc = 0;
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) sacc += LD(roff[i]);
+        long long tot;
+        block_excl_scan_ll(sacc, &tot);
+        if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+    }
+    if (!grid_barrier(ctl)) return;
+    if (blockIdx.x == 0) {
+        long long nbk = gridDim.x;
+        long long per = (nbk + blockDim.x - 1) / blockDim.x;
+        long long l0 = threadIdx.x * per, l1 = l0 + per < nbk ? l0 + per : nbk;
+        long long sacc = 0;
+        for (long long i = l0; i < l1; ++i) sacc += LD(bsum[i]);
+        long long tot;
+        long long pre = block_excl_scan_ll(sacc, &tot);
+        for (long long i = l0; i < l1; ++i) {
+            long long t = LD(bsum[i]);
+            bsum[i] = pre;
+            pre += t;
+        }
+        if (threadIdx.x == 0) roff[nd] = tot;
+    }
+    if (!grid_barrier(ctl)) return;
+    {
+        long long carry = LD(bsum[blockIdx.x]);
+        for (long long t0 = lo; t0 < hi; t0 += blockDim.x) {
+            long long i = t0 + threadIdx.x;
+            long long d = i < hi ? LD(roff[i]) : 0;
+            long long tot;
+            long long pre = block_excl_scan_ll(d, &tot);
+            if (i < hi) roff[i] = carry + pre;
+            carry += tot;
+        }
     }
 }
 
@@ -440,16 +484,19 @@ __global__ void k_active(const int *L, int use_list, long long cnt_static, Ctl *
     if (*(volatile int *)&ctl->skip) return;
     unsigned ep = ctl->epoch;
     long long cnt = use_list ? (long long)ctl->naff : cnt_static;
-    GS_LOOP(i, cnt) {
-        int v = use_list ? L[i] : (int)i;
-        int p = rep[v];
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += (long long)gridDim.x * blockDim.x) {
+        long long i = base + threadIdx.x;
         bool on = false;
-        int x = -1;
-        if (att_ep[p] == ep) {
-            x = att_x[p];
-            on = x != p;
+        int v = 0, p = 0, x = -1;
+        if (i < cnt) {
+            v = use_list ? L[i] : (int)i;
+            p = rep[v];
+            if (att_ep[p] == ep) {
+                x = att_x[p];
+                on = x != p;
+            }
         }
-        long long q = agg_append(&ctl->nact, on);
+        long long q = block_append(&ctl->nact, on);
         if (on) {
             int pv = parent[v];
             act[q] = v;
@@ -457,7 +504,7 @@ __global__ void k_active(const int *L, int use_list, long long cnt_static, Ctl *
             J0[v] = pv;
             mark[v] = v == x;
         }
-        if (rep_ep[p] == ep) rep[v] = newrep[p];
+        if (i < cnt && rep_ep[p] == ep) rep[v] = newrep[p];
     }
 }
 
@@ -546,7 +593,7 @@ static unsigned coop_blocks(const void *fn, int nsm, int cap_per_sm) {
     if (per > cap_per_sm) per = cap_per_sm;
     return (unsigned)(per * nsm);
 }
-unsigned coop_blocks_jump(int nsm) { return coop_blocks((const void *)k_jump, nsm, 4); }
+unsigned coop_blocks_jump(int nsm) { return coop_blocks((const void *)k_jump, nsm, 8); }
 unsigned coop_blocks_hook(int nsm) { return coop_blocks((const void *)k_boruvka, nsm, 4); }
 unsigned coop_blocks_orient(int nsm) { return coop_blocks((const void *)k_orient, nsm, 2); }
 unsigned coop_blocks_mark(int nsm) { return coop_blocks((const void *)k_mark, nsm, 4); }
@@ -565,12 +612,12 @@ cudaError_t launch_copy_parent(int n, const int *parent, int *J0, cudaStream_t s
     k_copy<<<gsz(n), BLK, 0, s>>>(n, parent, J0);
     return cudaGetLastError();
 }
-cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J0,
-                        int *J1, int *rep, int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g,
-                        cudaStream_t s) {
-    void *args[] = {(void *)&A, (void *)&use_list, (void *)&cnt_static, (void *)&ctl, (void *)&J0,
-                    (void *)&J1, (void *)&rep, (void *)&D, (void *)&mode, (void *)&rold, (void *)&w,
-                    (void *)&heavy, (void *)&g};
+cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J,
+                        int *rep, int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g,
+                        long long *roff, long long *bsum, cudaStream_t s) {
+    void *args[] = {(void *)&A, (void *)&use_list, (void *)&cnt_static, (void *)&ctl, (void *)&J,
+                    (void *)&rep, (void *)&D, (void *)&mode, (void *)&rold, (void *)&w, (void *)&heavy,
+                    (void *)&g, (void *)&roff, (void *)&bsum};
     return cudaLaunchCooperativeKernel((const void *)k_jump, d.coop_jump, BLK, args, 0, s);
 }
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,

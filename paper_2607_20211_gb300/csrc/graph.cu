@@ -310,99 +310,78 @@ __global__ void k_del_claim(const int *batch, long long len, Index ix, Csr g, u6
 }
 
 // Delete, cross-edge scan (key edges M = E(G) - E(F) - B, Algorithm 1,
-// restricted): one warp per listed vertex u streams u's row; a live
-// neighbour x in another piece gives the cross edge {u, x}.  The list holds
-// every vertex outside the heaviest piece H of its old tree, so each cross
-// edge has a listed endpoint; when both are listed the smaller id emits it.
-// Parallel edges between two pieces are reduced on the fly to the one with
-// the minimum key (the others can never be in the minimum spanning forest):
-// lanes of the warp with the same neighbour piece take the minimum first
-// (for a fixed u the key order is the order of x), then one lane per group
-// updates the pair table.  A pair that finds no table slot is emitted as a
-// plain candidate.
-// One warp-wide step of the scan: 32 consecutive entries of row u.
-__device__ __forceinline__ void scan_chunk(int u, int ru, int hp, long long o, long long j, long long used,
-                                           const Csr &g, const int *rep, PairTable pt, Ctl *ctl, u64 *ck,
-                                           int *ca, int *cb, u64 cand_cap) {
-    int lane = threadIdx.x & 31;
-    bool emit = false;
-    int x = -1, rx = -1;
-    if (j < used) {
-        x = __ldcs(&g.col[o + j]);
-        if (x >= 0) {
-            rx = rep[x];
-            if (rx != ru) emit = rx == hp || u < x;
-        }
-    }
-    unsigned m = __ballot_sync(0xffffffffu, emit);
-    bool raw = false;
-    if (emit) {
-        unsigned grp = __match_any_sync(m, rx);
-        unsigned xmin = __reduce_min_sync(grp, (unsigned)x);
-        if (lane == __ffs(grp) - 1) raw = !pair_min(pt.pk, pt.mk, pt.mask, ru, rx, ekey((uint32_t)u, xmin));
-        if (raw) x = (int)xmin;
-    }
-    long long p = agg_append(&ctl->ncand, raw);
-    if (raw) {
-        if ((u64)p < cand_cap) {
-            ck[p] = ekey((uint32_t)u, (uint32_t)x);
-            ca[p] = ru;
-            cb[p] = rx;
-        } else {
-            atomicOr(&ctl->err, ERR_CAPACITY);
-        }
-    }
-}
-
-// Rows longer than this are left to k_scan_long, which spreads one row over
-// the whole grid (a single warp on a hub row would serialise the batch).
-#define SCAN_LONG_ROW 2048
-
-__global__ void k_scan_rows(const int *D, Ctl *ctl, Csr g, const int *rep, const int *rold, const u64 *heavy,
-                            PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap, int *longrows) {
+// restricted).  The rows of the listed vertices D (every vertex outside the
+// heaviest piece of its cut tree) are flattened by the prefix sum roff, and
+// each warp takes 32 consecutive entries, whatever rows they fall in (load
+// balanced: a hub row is spread over many warps, short rows share a warp).
+// Lane e finds its row among the 32 rows starting at the row of the warp's
+// first entry (found by binary search).  A live neighbour x of u in another
+// piece gives the cross edge {u, x}; every cross edge has a listed endpoint
+// and, when both are listed, the smaller id emits it.  Parallel edges
+// between two pieces are reduced to the one with the minimum key, which is
+// the only one that can be in the minimum spanning forest: lanes holding the
+// same piece pair take the minimum first, then one lane updates the pair
+// table.  A pair that finds no table slot is emitted as a plain candidate.
+__global__ void k_scan_lb(const int *D, const long long *roff, Ctl *ctl, Csr g, const int *rep, const int *rold,
+                          const u64 *heavy, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap) {
     if (*(volatile int *)&ctl->skip) return;
-    long long nd = (long long)ctl->ndet;
-    int lane = threadIdx.x & 31;
-    long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    long long scanned = 0;
-    for (long long w = warp; w < nd; w += nw) {
-        int u = D[w];
-        long long o = g.off[u];
-        long long cap = g.off[u + 1] - o;
-        long long used = g.used[u];
-        if (used > cap) used = cap;
-        scanned += used;
-        if (used > SCAN_LONG_ROW) {
-            if (lane == 0) longrows[atomicAdd(&ctl->nlong, 1ull)] = u;
-            continue;
+    const long long nd = (long long)ctl->ndet;
+    if (nd == 0) return;
+    const long long E = roff[nd];
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    if (warp == 0 && lane == 0) atomicAdd((u64 *)&ctl->scanned, (u64)E);
+    for (long long t0 = warp * 32; t0 < E; t0 += nw * 32) {
+        long long r0 = 0;
+        if (lane == 0) {
+            long long lo = 0, hi = nd - 1;
+            while (lo < hi) {
+                long long mid = (lo + hi + 1) >> 1;
+                if (roff[mid] <= t0) lo = mid;
+                else hi = mid - 1;
+            }
+            r0 = lo;
         }
-        int ru = rep[u];
-        int hp = (int)(unsigned)heavy[rold[u]];
-        for (long long j0 = 0; j0 < used; j0 += 32)
-            scan_chunk(u, ru, hp, o, j0 + lane, used, g, rep, pt, ctl, ck, ca, cb, cand_cap);
-    }
-    if (lane == 0 && scanned) atomicAdd((u64 *)&ctl->scanned, (u64)scanned);
-}
-
-// The long rows, each split over all warps of the grid.
-__global__ void k_scan_long(Ctl *ctl, Csr g, const int *rep, const int *rold, const u64 *heavy, PairTable pt,
-                            u64 *ck, int *ca, int *cb, u64 cand_cap, const int *longrows) {
-    if (*(volatile int *)&ctl->skip) return;
-    long long nl = (long long)ctl->nlong;
-    int lane = threadIdx.x & 31;
-    long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long h = 0; h < nl; ++h) {
-        int u = longrows[h];
-        long long o = g.off[u];
-        long long cap = g.off[u + 1] - o;
-        long long used = g.used[u];
-        if (used > cap) used = cap;
-        int ru = rep[u];
-        int hp = (int)(unsigned)heavy[rold[u]];
-        for (long long j0 = warp * 32; j0 < used; j0 += nw * 32)
-            scan_chunk(u, ru, hp, o, j0 + lane, used, g, rep, pt, ctl, ck, ca, cb, cand_cap);
+        r0 = __shfl_sync(0xffffffffu, r0, 0);
+        const long long e = t0 + lane;
+        const long long wv = r0 + lane < nd ? roff[r0 + lane] : LLONG_MAX;
+        int c = 0;
+        for (int k = 0; k < 32; ++k) c += __shfl_sync(0xffffffffu, wv, k) <= e;
+        bool emit = false;
+        int u = 0, x = -1, ru = 0, rx = 0;
+        if (e < E) {
+            long long r = r0 + c - 1;
+            u = D[r];
+            long long j = e - __shfl_sync(0xffffffffu, wv, c - 1);
+            x = __ldcs(&g.col[g.off[u] + j]);
+            if (x >= 0) {
+                ru = rep[u];
+                rx = rep[x];
+                if (rx != ru) {
+                    int hp = (int)(unsigned)heavy[rold[u]];
+                    emit = rx == hp || u < x;
+                }
+            }
+        }
+        unsigned m = __ballot_sync(0xffffffffu, emit);
+        bool raw = false;
+        u64 key = 0;
+        if (emit) {
+            unsigned grp = __match_any_sync(m, ((u64)(unsigned)ru << 32) | (unsigned)rx);
+            key = group_min_u64(grp, ekey((uint32_t)u, (uint32_t)x));
+            if (lane == __ffs(grp) - 1) raw = !pair_min(pt.pk, pt.mk, pt.mask, ru, rx, key);
+        }
+        long long p = agg_append(&ctl->ncand, raw);
+        if (raw) {
+            if ((u64)p < cand_cap) {
+                ck[p] = key;
+                ca[p] = ru;
+                cb[p] = rx;
+            } else {
+                atomicOr(&ctl->err, ERR_CAPACITY);
+            }
+        }
     }
 }
 
@@ -576,11 +555,10 @@ cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u
     k_del_claim<<<gsz(len), BLK, 0, s>>>(batch, len, ix, g, ovf, parent, rep, ctl, aff_ep, cut_ep, cutlist);
     return cudaGetLastError();
 }
-cudaError_t launch_scan_rows(const Dev &d, const int *D, Ctl *ctl, Csr g, const int *rep, const int *rold,
-                             const u64 *heavy, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap,
-                             int *longrows, cudaStream_t s) {
-    k_scan_rows<<<d.grid, BLK, 0, s>>>(D, ctl, g, rep, rold, heavy, pt, ck, ca, cb, cand_cap, longrows);
-    k_scan_long<<<d.grid, BLK, 0, s>>>(ctl, g, rep, rold, heavy, pt, ck, ca, cb, cand_cap, longrows);
+cudaError_t launch_scan_rows(const Dev &d, const int *D, const long long *roff, Ctl *ctl, Csr g, const int *rep,
+                             const int *rold, const u64 *heavy, PairTable pt, u64 *ck, int *ca, int *cb,
+                             u64 cand_cap, cudaStream_t s) {
+    k_scan_lb<<<d.grid, BLK, 0, s>>>(D, roff, ctl, g, rep, rold, heavy, pt, ck, ca, cb, cand_cap);
     return cudaGetLastError();
 }
 cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, PairTable pt, u64 *ck, int *ca,
