@@ -32,6 +32,7 @@ struct drsf_ctx {
     void *alloc_ctx = nullptr;
     std::vector<Buf> bufs;
     bool poisoned = false;
+    int jump_sync = 1;   // root search: 1 synchronous doubling rounds, 0 in-place path halving
     int pending_einval = 0;
 
     Ctl *ctl = nullptr;
@@ -490,8 +491,8 @@ static drsf_status create_impl(drsf_ctx *h, const int32_t *edges, int64_t m, con
     // representatives of F by pointer jumping over all vertices
     CK(launch_copy_parent(n, h->parent, h->J0, s));
     Csr g0{h->off, h->used, h->col};
-    CK(launch_jump(h->dev, nullptr, 0, n, h->ctl, h->J0, h->rep, h->D, 0, h->rold, h->wgt, h->heavy, g0, h->roff,
-                   h->bsum, s));
+    CK(launch_jump(h->dev, nullptr, 0, n, h->ctl, h->J0, h->J1, h->rep, h->D, 0, h->rold, h->wgt, h->heavy, g0,
+                   h->roff, h->bsum, h->jump_sync, s));
     Ctl c{};
     CK(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -554,6 +555,9 @@ drsf_status drsf_create(int32_t n, const int32_t *edges, int64_t m, const int32_
     h->dev.coop_hook = coop_blocks_hook(nsm);
     h->dev.coop_orient = coop_blocks_orient(nsm);
     h->dev.coop_mark = coop_blocks_mark(nsm);
+    // DRSF_JUMP=halving selects the in-place path-halving root search
+    const char *jm = getenv("DRSF_JUMP");
+    h->jump_sync = (jm && strcmp(jm, "halving") == 0) ? 0 : 1;
     drsf_status st = create_impl(h, edges, m, parent, s);
     if (st != DRSF_OK) {
         destroy_all(h);
@@ -598,8 +602,8 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
         CK(launch_aff_collect(h->dev, h->n, h->rep, h->aff_ep, h->parent, h->J0, h->A, h->rold, ctl, s));
         prof_end(h, PH_AFF, 1, s);
         prof_begin(h, PH_JUMP, s);
-        CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->J0, h->rep, h->D, 1, h->rold, h->wgt, h->heavy, g, h->roff,
-                       h->bsum, s));
+        CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->J0, h->J1, h->rep, h->D, 1, h->rold, h->wgt, h->heavy, g,
+                       h->roff, h->bsum, h->jump_sync, s));
         prof_end(h, PH_JUMP, 1, s);
         prof_begin(h, PH_SCAN, s);
         CK(launch_scan_rows(h->dev, h->D, h->roff, ctl, g, h->rep, h->rold, h->heavy, h->pt, h->ck[0], h->ca[0],

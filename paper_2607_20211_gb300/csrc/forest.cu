@@ -88,33 +88,86 @@ __device__ __forceinline__ int find_halving(int *J, int v, Ctl *ctl) {
 // of row lengths), which keeps the scan small when a cut near the root
 // detaches most of a tree.  The listed rows D get an exclusive prefix sum of
 // their lengths in roff (roff[ndet] = total) for the load-balanced scan.
-__global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *rep, int *D,
-                       int mode, const int *rold, unsigned *w, u64 *heavy, Csr g, long long *roff,
-                       long long *bsum) {
+__global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1, int *rep,
+                       int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g, long long *roff,
+                       long long *bsum, int sync_rounds) {
     if (*(volatile int *)&ctl->skip) return;
     long long cnt = use_list ? (long long)ctl->naff : cnt_static;
-    for (long long i = gtid(); i < cnt; i += gstride()) {
-        int v = use_list ? A[i] : (int)i;
-        int root = find_halving(J, v, ctl);
-        J[v] = root;
-        rep[v] = root;
-        if (mode == 1) {
-            if (root == v) w[v] = 0;
-            if (rold[v] == v) heavy[v] = 0;
+    if (sync_rounds) {
+        // synchronous doubling J <- J o J (ping-pong) until no pointer moves
+        int *Jc = J, *Jn = J1;
+        int r = 0;
+        for (;; ++r) {
+            if (r >= MAX_ROUNDS) {
+                if (gtid() == 0) atomicOr(&ctl->err, ERR_ROUNDS);
+                return;
+            }
+            if (gtid() == 0) ctl->flag[(r + 1) % 3] = 0;
+            bool ch = false;
+            for (long long i = gtid(); i < cnt; i += gstride()) {
+                int v = use_list ? A[i] : (int)i;
+                int w0 = LD(Jc[v]);
+                int w2 = LD(Jc[w0]);
+                Jn[v] = w2;
+                ch |= (w2 != w0);
+            }
+            if (__syncthreads_or(ch) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
+            if (!grid_barrier(ctl)) return;
+            int again = *(volatile int *)&ctl->flag[r % 3];
+            int *t = Jc; Jc = Jn; Jn = t;
+            if (!again) break;
         }
+        for (long long i = gtid(); i < cnt; i += gstride()) {
+            int v = use_list ? A[i] : (int)i;
+            int root = LD(Jc[v]);
+            rep[v] = root;
+            if (mode == 1) {
+                if (root == v) w[v] = 0;
+                if (rold[v] == v) heavy[v] = 0;
+            }
+        }
+        if (gtid() == 0) ctl->jump_rounds = r + 1;
+    } else {
+        for (long long i = gtid(); i < cnt; i += gstride()) {
+            int v = use_list ? A[i] : (int)i;
+            int root = find_halving(J, v, ctl);
+            J[v] = root;
+            rep[v] = root;
+            if (mode == 1) {
+                if (root == v) w[v] = 0;
+                if (rold[v] == v) heavy[v] = 0;
+            }
+        }
+        if (gtid() == 0) ctl->jump_rounds = 1;
     }
-    if (gtid() == 0) ctl->jump_rounds = 1;
     if (mode == 0) return;
     if (!grid_barrier(ctl)) return;
-    for (long long i = gtid(); i < cnt; i += gstride()) {
-        int v = A[i];
-        int p = LD(rep[v]);
-        long long cap = g.off[v + 1] - g.off[v];
-        long long used = g.used[v];
-        unsigned d = (unsigned)(used < cap ? used : cap) + 1u;
-        unsigned grp = __match_any_sync(__activemask(), p);
-        unsigned tot = __reduce_add_sync(grp, d);
-        if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&w[p], tot);
+    {
+        // piece weights; the dominant piece of the block is summed in shared
+        // memory (one global atomic per block for it)
+        __shared__ int s_p;
+        __shared__ unsigned s_sum;
+        if (threadIdx.x == 0) {
+            s_p = -1;
+            s_sum = 0;
+        }
+        __syncthreads();
+        for (long long i = gtid(); i < cnt; i += gstride()) {
+            int v = A[i];
+            int p = LD(rep[v]);
+            long long cap = g.off[v + 1] - g.off[v];
+            long long used = g.used[v];
+            unsigned d = (unsigned)(used < cap ? used : cap) + 1u;
+            unsigned grp = __match_any_sync(__activemask(), p);
+            unsigned tot = __reduce_add_sync(grp, d);
+            if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
+                if (*(volatile int *)&s_p == -1) atomicCAS(&s_p, -1, p);
+                if (*(volatile int *)&s_p == p) atomicAdd(&s_sum, tot);
+                else atomicAdd(&w[p], tot);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && s_p != -1) atomicAdd(&w[s_p], s_sum);
     }
     if (!grid_barrier(ctl)) return;
     for (long long i = gtid(); i < cnt; i += gstride()) {
@@ -328,12 +381,20 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         }
     }
     if (!grid_barrier(ctl)) return;
-    // phase 2: smallest piece id per super-tree, degrees
+    // phase 2: smallest piece id per super-tree, degrees (lanes with the
+    // same target combine first: one super-tree or piece can collect most
+    // of the batch's edges)
     for (long long i = gtid(); i < 2 * ner; i += gstride()) {
         u64 k = a.er[i >> 1];
         int p = a.rep[(i & 1) ? khi(k) : klo(k)];
-        atomicMin(&a.minp[find_root(a.comp, p, ctl)], p);
-        atomicAdd(&a.pdeg[LD(a.pidx[p])], 1);
+        int root = find_root(a.comp, p, ctl);
+        unsigned act = __activemask();
+        unsigned g1 = __match_any_sync(act, root);
+        int pm = (int)__reduce_min_sync(g1, (unsigned)p);
+        if ((int)(threadIdx.x & 31) == __ffs(g1) - 1) atomicMin(&a.minp[root], pm);
+        int id = LD(a.pidx[p]);
+        unsigned g2 = __match_any_sync(act, id);
+        if ((int)(threadIdx.x & 31) == __ffs(g2) - 1) atomicAdd(&a.pdeg[id], __popc(g2));
     }
     if (!grid_barrier(ctl)) return;
     // phase 2b: leaf edges; core degrees
@@ -345,9 +406,13 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         bool leaf1 = LD(a.pdeg[id1]) == 1 && LD(a.minp[find_root(a.comp, p1, ctl)]) != p1;
         unsigned char lf = leaf0 ? 1 : (leaf1 ? 2 : 0);
         a.lf[i] = lf;
+        unsigned act = __activemask();
+        unsigned core = __ballot_sync(act, !lf);
         if (!lf) {
-            atomicAdd(&a.cdeg[id0], 1);
-            atomicAdd(&a.cdeg[id1], 1);
+            unsigned g0 = __match_any_sync(core, id0);
+            if ((int)(threadIdx.x & 31) == __ffs(g0) - 1) atomicAdd(&a.cdeg[id0], __popc(g0));
+            unsigned g1 = __match_any_sync(core, id1);
+            if ((int)(threadIdx.x & 31) == __ffs(g1) - 1) atomicAdd(&a.cdeg[id1], __popc(g1));
         }
     }
     if (!grid_barrier(ctl)) return;
@@ -392,11 +457,18 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
     if (!grid_barrier(ctl)) return;
     // phase 4: place core arcs; arc 2i = (lo-piece -> hi-piece), 2i+1 its twin
     for (long long i = gtid(); i < 2 * ner; i += gstride()) {
-        if (LD(a.lf[i >> 1])) continue;
+        bool core = !LD(a.lf[i >> 1]);
+        unsigned cm = __ballot_sync(__activemask(), core);
+        if (!core) continue;
         u64 k = a.er[i >> 1];
         int p = a.rep[(i & 1) ? khi(k) : klo(k)];
         int id = LD(a.pidx[p]);
-        int slot = LD(a.poff[id]) + atomicAdd(&a.pcur[id], 1);
+        unsigned grp = __match_any_sync(cm, id);
+        int lane = threadIdx.x & 31, leader = __ffs(grp) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&a.pcur[id], __popc(grp));
+        base = __shfl_sync(grp, base, leader);
+        int slot = LD(a.poff[id]) + base + __popc(grp & ((1u << lane) - 1u));
         a.adj[slot] = (int)i;
         a.apos[i] = slot;
     }
@@ -612,12 +684,12 @@ cudaError_t launch_copy_parent(int n, const int *parent, int *J0, cudaStream_t s
     k_copy<<<gsz(n), BLK, 0, s>>>(n, parent, J0);
     return cudaGetLastError();
 }
-cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J,
+cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1,
                         int *rep, int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g,
-                        long long *roff, long long *bsum, cudaStream_t s) {
-    void *args[] = {(void *)&A, (void *)&use_list, (void *)&cnt_static, (void *)&ctl, (void *)&J,
+                        long long *roff, long long *bsum, int sync_rounds, cudaStream_t s) {
+    void *args[] = {(void *)&A, (void *)&use_list, (void *)&cnt_static, (void *)&ctl, (void *)&J, (void *)&J1,
                     (void *)&rep, (void *)&D, (void *)&mode, (void *)&rold, (void *)&w, (void *)&heavy,
-                    (void *)&g, (void *)&roff, (void *)&bsum};
+                    (void *)&g, (void *)&roff, (void *)&bsum, (void *)&sync_rounds};
     return cudaLaunchCooperativeKernel((const void *)k_jump, d.coop_jump, BLK, args, 0, s);
 }
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
