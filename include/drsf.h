@@ -206,6 +206,16 @@ DRSF_API drsf_status drsf_profile_start(drsf_handle h, int64_t max_batches);
 DRSF_API drsf_status drsf_profile_stop(drsf_handle h, drsf_profile_t *out, drsf_stream stream);
 DRSF_API const char *drsf_phase_name(int phase);
 
+/*
+ * drsf_selftest_barrier_timeout -- failure-detection self-test (not part of
+ * the paper).  Launches a two-block cooperative kernel in which one block
+ * never reaches the grid barrier, so the other block's bounded wait (about
+ * two seconds) runs out.  Returns DRSF_ETIMEOUT when the wait gave up and
+ * reported it as designed, DRSF_OK if it did not time out, DRSF_ECUDA on a
+ * launch failure.  Synchronises `stream`; the CUDA context stays usable.
+ */
+DRSF_API drsf_status drsf_selftest_barrier_timeout(drsf_stream stream);
+
 /* drsf_destroy -- release all device memory (synchronises the handle's last
  * stream).  NULL is a no-op. */
 DRSF_API void drsf_destroy(drsf_handle h);

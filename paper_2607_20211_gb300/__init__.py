@@ -129,6 +129,8 @@ def _load():
         lib.drsf_profile_start.argtypes = [vp, i64]
         lib.drsf_profile_stop.restype = ctypes.c_int
         lib.drsf_profile_stop.argtypes = [vp, P(Profile), vp]
+        lib.drsf_selftest_barrier_timeout.restype = ctypes.c_int
+        lib.drsf_selftest_barrier_timeout.argtypes = [vp]
         lib.drsf_phase_name.restype = ctypes.c_char_p
         lib.drsf_phase_name.argtypes = [ctypes.c_int]
         _lib = lib
@@ -150,6 +152,11 @@ def use_torch_allocator(enable: bool = True) -> None:
         st = lib.drsf_set_allocator(_ALLOC_FN(), _FREE_FN(), None)
     if st:
         raise DRSFError(st, "drsf_set_allocator")
+
+
+def selftest_barrier_timeout(stream=None) -> int:
+    """Run the bounded-wait self-test; returns the status (ETIMEOUT expected)."""
+    return int(_load().drsf_selftest_barrier_timeout(_stream_ptr(stream)))
 
 
 def _stream_ptr(stream) -> int:

@@ -835,6 +835,23 @@ const char *drsf_phase_name(int phase) {
     return phase >= 0 && phase < DRSF_NUM_PHASES ? kPhaseNames[phase] : "?";
 }
 
+drsf_status drsf_selftest_barrier_timeout(drsf_stream stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctl *ctl = nullptr;
+    CK(cudaMalloc(&ctl, sizeof(Ctl)));
+    CK(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    cudaError_t e = launch_barrier_selftest(ctl, s);
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(ctl);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return DRSF_ECUDA;
+    }
+    return (err & ERR_TIMEOUT) ? DRSF_ETIMEOUT : DRSF_OK;
+}
+
 void drsf_destroy(drsf_handle h) { destroy_all(h); }
 
 const char *drsf_error_string(drsf_status s) {

@@ -43,8 +43,7 @@ struct Ctl {
     int skip;               // current batch rejected (ERR_BATCH_ID seen)
     unsigned epoch;         // batch counter; epoch stamps compare against it
     int op;
-    unsigned bar_count;
-    unsigned bar_gen;
+    u64 bar[4];             // grid-barrier counters: jump, hook, orient, mark
     int flag[3];            // per-round "another round needed" flags
     u64 cnt[3];             // per-round list sizes (hook-and-compress)
     u64 nb;                 // normalised batch edges (new / deleted keys)
@@ -224,38 +223,44 @@ __device__ __forceinline__ u64 globaltimer_ns() {
     return t;
 }
 
+__device__ __forceinline__ u64 ld_acquire_u64(const u64 *p) {
+    u64 v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Grid-wide barrier for cooperative launches (all blocks co-resident).
-// Generation-counting barrier; the wait is bounded: after
-// BARRIER_TIMEOUT_NS it latches ERR_TIMEOUT and every block returns false
-// from then on, so the kernel unwinds instead of hanging.
-__device__ __forceinline__ bool grid_barrier(Ctl *ctl) {
+// Ticket barrier on a monotonic counter owned by one kernel (always launched
+// with the same block count, so the counter is a multiple of gridDim.x
+// between barriers): each block takes a ticket t and waits until the counter
+// reaches the end of t's group.  The wait is bounded: after
+// BARRIER_TIMEOUT_NS it latches ERR_TIMEOUT and returns false, and a block
+// that sees another block's timeout returns false too, so the kernel unwinds
+// instead of hanging.
+__device__ __forceinline__ bool grid_barrier(Ctl *ctl, u64 *bar) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *vgen = &ctl->bar_gen;
-        volatile int *verr = &ctl->err;
-        unsigned g = *vgen;
+        const u64 nb = gridDim.x;
         __threadfence();
-        unsigned prev = atomicAdd(&ctl->bar_count, 1u);
+        u64 t = atomicAdd(bar, 1ull);
+        u64 target = (t / nb + 1) * nb;
         int ok = 1;
-        if (prev == gridDim.x - 1) {
-            atomicExch(&ctl->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
+        if (ld_acquire_u64(bar) < target) {
             u64 t0 = globaltimer_ns();
-            while (*vgen == g) {
-                if (*verr & ERR_TIMEOUT) { ok = 0; break; }
-                if (globaltimer_ns() - t0 > BARRIER_TIMEOUT_NS) {
-                    atomicOr(&ctl->err, ERR_TIMEOUT);
-                    ok = 0;
-                    break;
+            unsigned it = 0;
+            while (ld_acquire_u64(bar) < target) {
+                if ((++it & 255u) == 0) {
+                    if (*(volatile int *)&ctl->err & ERR_TIMEOUT) { ok = 0; break; }
+                    if (globaltimer_ns() - t0 > BARRIER_TIMEOUT_NS) {
+                        atomicOr(&ctl->err, ERR_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
                 }
-                __nanosleep(32);
             }
         }
-        __threadfence();
-        s_ok = ok && !(*verr & ERR_TIMEOUT);
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;

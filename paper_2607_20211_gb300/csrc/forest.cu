@@ -112,7 +112,7 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
                 ch |= (w2 != w0);
             }
             if (__syncthreads_or(ch) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
-            if (!grid_barrier(ctl)) return;
+            if (!grid_barrier(ctl, &ctl->bar[0])) return;
             int again = *(volatile int *)&ctl->flag[r % 3];
             int *t = Jc; Jc = Jn; Jn = t;
             if (!again) break;
@@ -141,7 +141,7 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
         if (gtid() == 0) ctl->jump_rounds = 1;
     }
     if (mode == 0) return;
-    if (!grid_barrier(ctl)) return;
+    if (!grid_barrier(ctl, &ctl->bar[0])) return;
     {
         // piece weights; the dominant piece of the block is summed in shared
         // memory (one global atomic per block for it)
@@ -169,12 +169,12 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
         __syncthreads();
         if (threadIdx.x == 0 && s_p != -1) atomicAdd(&w[s_p], s_sum);
     }
-    if (!grid_barrier(ctl)) return;
+    if (!grid_barrier(ctl, &ctl->bar[0])) return;
     for (long long i = gtid(); i < cnt; i += gstride()) {
         int v = A[i];
         if (LD(rep[v]) == v) atomicMax(&heavy[rold[v]], ((u64)LD(w[v]) << 32) | (unsigned)v);
     }
-    if (!grid_barrier(ctl)) return;
+    if (!grid_barrier(ctl, &ctl->bar[0])) return;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += gstride()) {
         long long i = base + threadIdx.x;
         bool scan = false;
@@ -194,7 +194,7 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
             roff[p] = len;
         }
     }
-    if (!grid_barrier(ctl)) return;
+    if (!grid_barrier(ctl, &ctl->bar[0])) return;
     // exclusive scan of roff[0..nd) in place: chunk sums, scan of the sums,
     // chunk rescans
     const long long nd = (long long)*(volatile u64 *)&ctl->ndet;
@@ -207,7 +207,7 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
         block_excl_scan_ll(sacc, &tot);
         if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
     }
-    if (!grid_barrier(ctl)) return;
+    if (!grid_barrier(ctl, &ctl->bar[0])) return;
     if (blockIdx.x == 0) {
         long long nbk = gridDim.x;
         long long per = (nbk + blockDim.x - 1) / blockDim.x;
@@ -223,7 +223,7 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
         }
         if (threadIdx.x == 0) roff[nd] = tot;
     }
-    if (!grid_barrier(ctl)) return;
+    if (!grid_barrier(ctl, &ctl->bar[0])) return;
     {
         long long carry = LD(bsum[blockIdx.x]);
         for (long long t0 = lo; t0 < hi; t0 += blockDim.x) {
@@ -261,7 +261,7 @@ __global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int 
         ctl->cnt[1] = ctl->cnt[2] = 0;
         ctl->flag[0] = ctl->flag[1] = ctl->flag[2] = 0;
     }
-    if (!grid_barrier(ctl)) return;
+    if (!grid_barrier(ctl, &ctl->bar[1])) return;
     int r = 0;
     for (;; ++r) {
         if (r >= MAX_ROUNDS) {
@@ -286,7 +286,7 @@ __global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int 
             warp_atomic_min_u64(best, a, k, a != b);
             warp_atomic_min_u64(best, b, k, a != b);
         }
-        if (!grid_barrier(ctl)) return;
+        if (!grid_barrier(ctl, &ctl->bar[1])) return;
         // phase B: hook along minimum edges, keep the rest
         bool hooked = false;
         for (long long i = gtid(); i < c; i += gstride()) {
@@ -318,7 +318,7 @@ __global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int 
             }
         }
         if (__syncthreads_or(hooked) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
-        if (!grid_barrier(ctl)) return;
+        if (!grid_barrier(ctl, &ctl->bar[1])) return;
         if (!*(volatile int *)&ctl->flag[r % 3]) break;
     }
     if (gtid() == 0) ctl->hook_rounds = r;
@@ -380,7 +380,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
             a.pcur[id] = 0;
         }
     }
-    if (!grid_barrier(ctl)) return;
+    if (!grid_barrier(ctl, &ctl->bar[2])) return;
     // phase 2: smallest piece id per super-tree, degrees (lanes with the
     // same target combine first: one super-tree or piece can collect most
     // of the batch's edges)
@@ -396,7 +396,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         unsigned g2 = __match_any_sync(act, id);
         if ((int)(threadIdx.x & 31) == __ffs(g2) - 1) atomicAdd(&a.pdeg[id], __popc(g2));
     }
-    if (!grid_barrier(ctl)) return;
+    if (!grid_barrier(ctl, &ctl->bar[2])) return;
     // phase 2b: leaf edges; core degrees
     for (long long i = gtid(); i < ner; i += gstride()) {
         u64 k = a.er[i];
@@ -415,7 +415,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
             if ((int)(threadIdx.x & 31) == __ffs(g1) - 1) atomicAdd(&a.cdeg[id1], __popc(g1));
         }
     }
-    if (!grid_barrier(ctl)) return;
+    if (!grid_barrier(ctl, &ctl->bar[2])) return;
     // phase 3: exclusive scan of core degrees -> adjacency offsets
     const long long np = (long long)*(volatile u64 *)&ctl->npc;
     const long long chunk = (np + gridDim.x - 1) / gridDim.x;
@@ -427,7 +427,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         block_excl_scan(s, &tot);
         if (threadIdx.x == 0) a.bsum[blockIdx.x] = tot;
     }
-    if (!grid_barrier(ctl)) return;
+    if (!grid_barrier(ctl, &ctl->bar[2])) return;
     if (blockIdx.x == 0) {
         long long nbk = gridDim.x;
         long long per = (nbk + BLK - 1) / BLK;
@@ -442,7 +442,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
             pre += (int)t;
         }
     }
-    if (!grid_barrier(ctl)) return;
+    if (!grid_barrier(ctl, &ctl->bar[2])) return;
     {
         int carry = (int)LD(a.bsum[blockIdx.x]);
         for (long long t0 = lo; t0 < hi; t0 += blockDim.x) {
@@ -454,7 +454,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
             carry += tot;
         }
     }
-    if (!grid_barrier(ctl)) return;
+    if (!grid_barrier(ctl, &ctl->bar[2])) return;
     // phase 4: place core arcs; arc 2i = (lo-piece -> hi-piece), 2i+1 its twin
     for (long long i = gtid(); i < 2 * ner; i += gstride()) {
         bool core = !LD(a.lf[i >> 1]);
@@ -472,7 +472,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         a.adj[slot] = (int)i;
         a.apos[i] = slot;
     }
-    if (!grid_barrier(ctl)) return;
+    if (!grid_barrier(ctl, &ctl->bar[2])) return;
     // phase 5: Euler successors of core arcs; open the circuit at each root
     for (long long i = gtid(); i < 2 * ner; i += gstride()) {
         if (LD(a.lf[i >> 1])) continue;
@@ -492,7 +492,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         a.nx0[i] = succ;
         a.val0[i] = 1;
     }
-    if (!grid_barrier(ctl)) return;
+    if (!grid_barrier(ctl, &ctl->bar[2])) return;
     // phase 6: list ranking (Wyllie): val = arcs from here to the tour end
     int *vc = a.val0, *vn = a.val1, *nc = a.nx0, *nn = a.nx1;
     int r = 0;
@@ -516,7 +516,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
             }
         }
         if (__syncthreads_or(ch) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
-        if (!grid_barrier(ctl)) return;
+        if (!grid_barrier(ctl, &ctl->bar[2])) return;
         int again = *(volatile int *)&ctl->flag[r % 3];
         int *t = vc; vc = vn; vn = t;
         t = nc; nc = nn; nn = t;
@@ -607,7 +607,7 @@ __global__ void k_mark(Ctl *ctl, const int *act, int *J0, int *J1, unsigned char
             more |= parent[w2] != w2;
         }
         if (__syncthreads_or(more) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
-        if (!grid_barrier(ctl)) return;
+        if (!grid_barrier(ctl, &ctl->bar[3])) return;
         int again = *(volatile int *)&ctl->flag[r % 3];
         int *t = Jc; Jc = Jn; Jn = t;
         if (!again) break;
@@ -653,6 +653,13 @@ __global__ void k_label_min(int n, const int *rep, int *tmp) {
 }
 __global__ void k_label_out(int n, const int *rep, const int *tmp, int *out) {
     GS_LOOP(v, n) out[v] = tmp[rep[v]];
+}
+
+// Failure-detection self-test: block 1 never arrives at the barrier, so
+// block 0's bounded wait runs out, latches ERR_TIMEOUT and returns.
+__global__ void k_barrier_selftest(Ctl *ctl) {
+    if (blockIdx.x != 0) return;
+    grid_barrier(ctl, &ctl->bar[0]);
 }
 
 // ------------------------------------------------------------- wrappers
@@ -726,4 +733,8 @@ cudaError_t launch_labels(int n, const int *rep, int *tmp, int *out, cudaStream_
     k_label_min<<<gsz(n), BLK, 0, s>>>(n, rep, tmp);
     k_label_out<<<gsz(n), BLK, 0, s>>>(n, rep, tmp, out);
     return cudaGetLastError();
+}
+cudaError_t launch_barrier_selftest(Ctl *ctl, cudaStream_t s) {
+    void *args[] = {(void *)&ctl};
+    return cudaLaunchCooperativeKernel((const void *)k_barrier_selftest, 2, 32, args, 0, s);
 }

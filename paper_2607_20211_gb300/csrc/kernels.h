@@ -88,3 +88,4 @@ unsigned coop_blocks_jump(int nsm);
 unsigned coop_blocks_hook(int nsm);
 unsigned coop_blocks_orient(int nsm);
 unsigned coop_blocks_mark(int nsm);
+cudaError_t launch_barrier_selftest(Ctl *ctl, cudaStream_t s);
