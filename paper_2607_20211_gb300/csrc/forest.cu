@@ -128,6 +128,8 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
         }
         if (gtid() == 0) ctl->jump_rounds = r + 1;
     } else {
+        // J[v] may later be overwritten by another walk's halving step with
+        // a non-root ancestor; rep[v] takes this thread's own result.
         for (long long i = gtid(); i < cnt; i += gstride()) {
             int v = use_list ? A[i] : (int)i;
             int root = find_halving(J, v, ctl);
