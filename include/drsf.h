@@ -216,6 +216,29 @@ DRSF_API const char *drsf_phase_name(int phase);
  */
 DRSF_API drsf_status drsf_selftest_barrier_timeout(drsf_stream stream);
 
+/*
+ * drsf_forest_labels_noalloc -- the labels of drsf_labels (smallest vertex
+ * id of each tree) for a forest the caller passes as a parent array, with no
+ * device memory allocated by the call: all scratch lives in one fixed
+ * device array compiled into the library.  The paper has no counterpart; it
+ * is for callers that cannot allocate when they need the answer (a device
+ * memory budget reserved up front, code running inside an allocator or its
+ * callbacks, latency-bound loops where cudaMalloc would synchronise).
+ *   n       1 <= n <= DRSF_NOALLOC_MAX_N, else DRSF_EINVAL (nothing enqueued)
+ *   parent  device, int32[n], parent[r] == r at roots
+ *   labels  device, int32[n], output
+ * Synchronises `stream`; returns DRSF_EINVAL if parent has an id outside
+ * [0, n) or a cycle.  Every call on a device shares the scratch array (it
+ * keeps the last call's contents; each call re-initialises what it reads):
+ * calls that overlap on the GPU race, so order them on one stream.  The
+ * first call on a device resolves the array's device address with that
+ * device current; make it before any stream capture.  The array (12 MiB)
+ * stays allocated on every GPU that loads the library until exit.
+ */
+#define DRSF_NOALLOC_MAX_N (1 << 20)
+DRSF_API drsf_status drsf_forest_labels_noalloc(int32_t n, const int32_t *parent, int32_t *labels,
+                                               drsf_stream stream);
+
 /* drsf_destroy -- release all device memory (synchronises the handle's last
  * stream).  NULL is a no-op. */
 DRSF_API void drsf_destroy(drsf_handle h);
