@@ -596,10 +596,11 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
         // Algorithm 1, delete: remove B, cut tree edges, re-label the cut trees
         prof_begin(h, PH_DEL_CLAIM, s);
         CK(launch_del_claim(batch, len, h->ix, g, h->ovf, h->parent, h->rep, ctl, h->aff_ep, h->cut_ep,
-                            h->cutlist, s));
+                            h->cutlist, h->wgt, s));
         prof_end(h, PH_DEL_CLAIM, len > 0 ? 1 : 0, s);
         prof_begin(h, PH_AFF, s);
-        CK(launch_aff_collect(h->dev, h->n, h->rep, h->aff_ep, h->parent, h->J0, h->A, h->rold, ctl, s));
+        CK(launch_aff_collect(h->dev, h->n, h->rep, h->aff_ep, h->parent, h->J0, h->A, h->rold, h->wgt, h->heavy,
+                              ctl, s));
         prof_end(h, PH_AFF, 1, s);
         prof_begin(h, PH_JUMP, s);
         CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->J0, h->J1, h->rep, h->D, 1, h->rold, h->wgt, h->heavy, g,

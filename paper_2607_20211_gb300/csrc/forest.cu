@@ -43,7 +43,7 @@ __global__ void k_begin(Ctl *ctl, int op, long long len) {
 // Delete: list the vertices of every tree that lost a tree edge (its old
 // root was stamped by the cut) and seed J0 = parent (the cut forest F^).
 __global__ void k_aff_collect(int n, const int *rep, const unsigned *aff_ep, const int *parent, int *J0, int *A,
-                              int *rold, Ctl *ctl) {
+                              int *rold, unsigned *w, u64 *heavy, Ctl *ctl) {
     if (*(volatile int *)&ctl->skip) return;
     unsigned ep = ctl->epoch;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
@@ -55,6 +55,10 @@ __global__ void k_aff_collect(int n, const int *rep, const unsigned *aff_ep, con
             A[p] = (int)v;
             J0[v] = parent[v];
             rold[v] = r;
+            if (r == (int)v) {   // the old root: piece-weight and heaviest-piece slots
+                w[v] = 0;
+                heavy[v] = 0;
+            }
         }
     }
 }
@@ -94,7 +98,10 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
     if (*(volatile int *)&ctl->skip) return;
     long long cnt = use_list ? (long long)ctl->naff : cnt_static;
     if (sync_rounds) {
-        // synchronous doubling J <- J o J (ping-pong) until no pointer moves
+        // synchronous doubling J <- J o J (ping-pong).  A pointer that has
+        // reached a root is stored complemented (negative): a converged
+        // vertex skips the gather, and the loop ends in the first round in
+        // which every listed vertex is converged (no verification round).
         int *Jc = J, *Jn = J1;
         int r = 0;
         for (;; ++r) {
@@ -103,50 +110,42 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
                 return;
             }
             if (gtid() == 0) ctl->flag[(r + 1) % 3] = 0;
-            bool ch = false;
+            bool open = false;
             for (long long i = gtid(); i < cnt; i += gstride()) {
                 int v = use_list ? A[i] : (int)i;
                 int w0 = LD(Jc[v]);
-                int w2 = LD(Jc[w0]);
-                Jn[v] = w2;
-                ch |= (w2 != w0);
+                int nv;
+                if (w0 < 0) {
+                    nv = w0;
+                } else {
+                    int w2 = LD(Jc[w0]);
+                    if (w2 < 0) nv = w2;
+                    else if (w2 == w0) nv = ~w0;
+                    else {
+                        nv = w2;
+                        open = true;
+                    }
+                }
+                Jn[v] = nv;
             }
-            if (__syncthreads_or(ch) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
+            if (__syncthreads_or(open) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
             if (!grid_barrier(ctl, &ctl->bar[0])) return;
             int again = *(volatile int *)&ctl->flag[r % 3];
             int *t = Jc; Jc = Jn; Jn = t;
             if (!again) break;
         }
-        for (long long i = gtid(); i < cnt; i += gstride()) {
-            int v = use_list ? A[i] : (int)i;
-            int root = LD(Jc[v]);
-            rep[v] = root;
-            if (mode == 1) {
-                if (root == v) w[v] = 0;
-                if (rold[v] == v) heavy[v] = 0;
-            }
-        }
         if (gtid() == 0) ctl->jump_rounds = r + 1;
-    } else {
-        // J[v] may later be overwritten by another walk's halving step with
-        // a non-root ancestor; rep[v] takes this thread's own result.
-        for (long long i = gtid(); i < cnt; i += gstride()) {
-            int v = use_list ? A[i] : (int)i;
-            int root = find_halving(J, v, ctl);
-            J[v] = root;
-            rep[v] = root;
-            if (mode == 1) {
-                if (root == v) w[v] = 0;
-                if (rold[v] == v) heavy[v] = 0;
+        if (mode == 0) {
+            for (long long i = gtid(); i < cnt; i += gstride()) {
+                int v = use_list ? A[i] : (int)i;
+                rep[v] = ~LD(Jc[v]);
             }
+            return;
         }
-        if (gtid() == 0) ctl->jump_rounds = 1;
-    }
-    if (mode == 0) return;
-    if (!grid_barrier(ctl, &ctl->bar[0])) return;
-    {
-        // piece weights; the dominant piece of the block is summed in shared
-        // memory (one global atomic per block for it)
+        // final pass: representatives and piece weights (sum of row lengths
+        // + 1 per vertex; weights of piece roots were zeroed at the cut);
+        // the dominant piece of the block is summed in shared memory (one
+        // global atomic per block for it)
         __shared__ int s_p;
         __shared__ unsigned s_sum;
         if (threadIdx.x == 0) {
@@ -156,7 +155,8 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
         __syncthreads();
         for (long long i = gtid(); i < cnt; i += gstride()) {
             int v = A[i];
-            int p = LD(rep[v]);
+            int p = ~LD(Jc[v]);
+            rep[v] = p;
             long long cap = g.off[v + 1] - g.off[v];
             long long used = g.used[v];
             unsigned d = (unsigned)(used < cap ? used : cap) + 1u;
@@ -170,6 +170,26 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
         }
         __syncthreads();
         if (threadIdx.x == 0 && s_p != -1) atomicAdd(&w[s_p], s_sum);
+    } else {
+        // J[v] may later be overwritten by another walk's halving step with
+        // a non-root ancestor; rep[v] takes this thread's own result.
+        for (long long i = gtid(); i < cnt; i += gstride()) {
+            int v = use_list ? A[i] : (int)i;
+            int root = find_halving(J, v, ctl);
+            J[v] = root;
+            rep[v] = root;
+        }
+        if (gtid() == 0) ctl->jump_rounds = 1;
+        if (mode == 0) return;
+        if (!grid_barrier(ctl, &ctl->bar[0])) return;
+        for (long long i = gtid(); i < cnt; i += gstride()) {
+            int v = A[i];
+            int p = LD(rep[v]);
+            long long cap = g.off[v + 1] - g.off[v];
+            long long used = g.used[v];
+            unsigned d = (unsigned)(used < cap ? used : cap) + 1u;
+            atomicAdd(&w[p], d);
+        }
     }
     if (!grid_barrier(ctl, &ctl->bar[0])) return;
     for (long long i = gtid(); i < cnt; i += gstride()) {
@@ -684,8 +704,8 @@ cudaError_t launch_begin(Ctl *ctl, int op, long long len, cudaStream_t s) {
     return cudaGetLastError();
 }
 cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, const int *parent,
-                               int *J0, int *A, int *rold, Ctl *ctl, cudaStream_t s) {
-    k_aff_collect<<<gsz(n), BLK, 0, s>>>(n, rep, aff_ep, parent, J0, A, rold, ctl);
+                               int *J0, int *A, int *rold, unsigned *w, u64 *heavy, Ctl *ctl, cudaStream_t s) {
+    k_aff_collect<<<gsz(n), BLK, 0, s>>>(n, rep, aff_ep, parent, J0, A, rold, w, heavy, ctl);
     (void)d;
     return cudaGetLastError();
 }

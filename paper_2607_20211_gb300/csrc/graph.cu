@@ -271,7 +271,8 @@ __global__ void k_ins_place(const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, 
 // orientation).  The old root of a cut tree is stamped "affected"; the cut
 // vertex becomes a piece root and is stamped in cut_ep.
 __global__ void k_del_claim(const int *batch, long long len, Index ix, Csr g, u64 *ovf, int *parent,
-                            const int *rep, Ctl *ctl, unsigned *aff_ep, unsigned *cut_ep, int *cutlist) {
+                            const int *rep, Ctl *ctl, unsigned *aff_ep, unsigned *cut_ep, int *cutlist,
+                            unsigned *w) {
     if (*(volatile int *)&ctl->skip) return;
     unsigned ep = ctl->epoch;
     GS_LOOP(i, len) {
@@ -296,6 +297,7 @@ __global__ void k_del_claim(const int *batch, long long len, Index ix, Csr g, u6
                     parent[c] = c;
                     cut_ep[c] = ep;
                     aff_ep[rep[c]] = ep;
+                    w[c] = 0;   // c roots a new piece: its weight slot
                 }
             }
         }
@@ -332,26 +334,30 @@ __global__ void k_scan_lb(const int *D, const long long *roff, Ctl *ctl, Csr g, 
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     if (warp == 0 && lane == 0) atomicAdd((u64 *)&ctl->scanned, (u64)E);
-    for (long long t0 = warp * 32; t0 < E; t0 += nw * 32) {
-        long long r0 = 0;
-        if (lane == 0) {
-            long long lo = 0, hi = nd - 1;
-            while (lo < hi) {
-                long long mid = (lo + hi + 1) >> 1;
-                if (roff[mid] <= t0) lo = mid;
-                else hi = mid - 1;
-            }
-            r0 = lo;
+    // this warp's contiguous range of entries, whole tiles of 32
+    const long long per = ((E + nw - 1) / nw + 31) & ~31ll;
+    const long long e_lo = warp * per, e_hi = e_lo + per < E ? e_lo + per : E;
+    if (e_lo >= e_hi) return;
+    long long r0 = 0;
+    if (lane == 0) {
+        long long lo = 0, hi = nd - 1;
+        while (lo < hi) {
+            long long mid = (lo + hi + 1) >> 1;
+            if (roff[mid] <= e_lo) lo = mid;
+            else hi = mid - 1;
         }
-        r0 = __shfl_sync(0xffffffffu, r0, 0);
+        r0 = lo;
+    }
+    r0 = __shfl_sync(0xffffffffu, r0, 0);
+    for (long long t0 = e_lo; t0 < e_hi; t0 += 32) {
         const long long e = t0 + lane;
         const long long wv = r0 + lane < nd ? roff[r0 + lane] : LLONG_MAX;
         int c = 0;
         for (int k = 0; k < 32; ++k) c += __shfl_sync(0xffffffffu, wv, k) <= e;
+        const long long r = r0 + c - 1;
         bool emit = false;
         int u = 0, x = -1, ru = 0, rx = 0;
-        if (e < E) {
-            long long r = r0 + c - 1;
+        if (e < e_hi) {
             u = D[r];
             long long j = e - __shfl_sync(0xffffffffu, wv, c - 1);
             x = __ldcs(&g.col[g.off[u] + j]);
@@ -364,6 +370,8 @@ __global__ void k_scan_lb(const int *D, const long long *roff, Ctl *ctl, Csr g, 
                 }
             }
         }
+        // next tile starts in the row of this tile's last entry
+        r0 = __shfl_sync(0xffffffffu, r, 31);
         unsigned m = __ballot_sync(0xffffffffu, emit);
         bool raw = false;
         u64 key = 0;
@@ -550,9 +558,9 @@ cudaError_t launch_ins_place(const Dev &d, const u64 *nkey, const u64 *nslot, Ct
 }
 cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u64 *ovf, int *parent,
                              const int *rep, Ctl *ctl, unsigned *aff_ep, unsigned *cut_ep, int *cutlist,
-                             cudaStream_t s) {
+                             unsigned *w, cudaStream_t s) {
     if (len <= 0) return cudaSuccess;
-    k_del_claim<<<gsz(len), BLK, 0, s>>>(batch, len, ix, g, ovf, parent, rep, ctl, aff_ep, cut_ep, cutlist);
+    k_del_claim<<<gsz(len), BLK, 0, s>>>(batch, len, ix, g, ovf, parent, rep, ctl, aff_ep, cut_ep, cutlist, w);
     return cudaGetLastError();
 }
 cudaError_t launch_scan_rows(const Dev &d, const int *D, const long long *roff, Ctl *ctl, Csr g, const int *rep,

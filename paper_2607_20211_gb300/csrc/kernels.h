@@ -32,7 +32,7 @@ cudaError_t launch_ins_place(const Dev &d, const u64 *nkey, const u64 *nslot, Ct
                              cudaStream_t s);
 cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u64 *ovf, int *parent,
                              const int *rep, Ctl *ctl, unsigned *aff_ep, unsigned *cut_ep, int *cutlist,
-                             cudaStream_t s);
+                             unsigned *w, cudaStream_t s);
 struct PairTable {
     u64 *pk;   // piece pair key, EMPTY_KEY when free
     u64 *mk;   // minimum edge key of the pair
@@ -53,7 +53,7 @@ cudaError_t launch_check_cross(const int *pairs, long long m, const int *rep, in
 // forest.cu ------------------------------------------------------------
 cudaError_t launch_begin(Ctl *ctl, int op, long long len, cudaStream_t s);
 cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, const int *parent,
-                               int *J0, int *A, int *rold, Ctl *ctl, cudaStream_t s);
+                               int *J0, int *A, int *rold, unsigned *w, u64 *heavy, Ctl *ctl, cudaStream_t s);
 cudaError_t launch_copy_parent(int n, const int *parent, int *J0, cudaStream_t s);
 cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1,
                         int *rep, int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g,
