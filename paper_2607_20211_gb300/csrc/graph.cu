@@ -370,8 +370,15 @@ __global__ void k_scan_lb(const int *D, const long long *roff, Ctl *ctl, Csr g, 
                 }
             }
         }
-        // next tile starts in the row of this tile's last entry
-        r0 = __shfl_sync(0xffffffffu, r, 31);
+        // the next tile starts at t0 + 32: in the row of this tile's last
+        // entry or the one after it (rows are never empty); the window of
+        // the next tile must start exactly at that row
+        {
+            long long r31 = __shfl_sync(0xffffffffu, r, 31);
+            long long nx = r31;
+            if (lane == 31 && r31 + 1 < nd && roff[r31 + 1] <= t0 + 32) nx = r31 + 1;
+            r0 = __shfl_sync(0xffffffffu, nx, 31);
+        }
         unsigned m = __ballot_sync(0xffffffffu, emit);
         bool raw = false;
         u64 key = 0;

@@ -43,6 +43,13 @@ def test_rmat16_trajectory():
     run_trajectory(g, [(I, 1000), (D, 1000), (I, 10_000), (D, 10_000)] * 3, seed=3)
 
 
+def test_sparse_rows_scan():
+    """Average degree ~2: delete scans cover long runs of one- and two-entry
+    rows, so scan tiles span many rows."""
+    g = workloads.er_graph(200_000, 200_000, seed=17)
+    run_trajectory(g, [(D, 20_000), (I, 20_000)] * 3, seed=18, tree_frac=0.7)
+
+
 def test_grid_deep_paths():
     """Grid 512 x 512, p = 0.6, deletes with 90% tree edges (long reversals),
     local inserts within 64 cells."""
