@@ -54,6 +54,7 @@ struct Ctl {
     u64 ner;                // replacement edges
     u64 npc;                // distinct pieces touched by E_r
     u64 nact;               // active vertices (path reversal)
+    u64 ncore;              // core arcs of the super-forest Euler tour
     u64 ovf_count;          // overflow list length (grows until rebuild)
     long long edges;        // live undirected edges of G
     long long htomb;        // index tombstones

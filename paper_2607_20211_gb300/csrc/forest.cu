@@ -17,6 +17,10 @@
 
 #include "kernels.h"
 
+// cores of up to this many arcs are list-ranked in one block's shared memory
+#define ORIENT_SMEM_ARCS 12288
+#define ORIENT_SMEM_BYTES (4 * ORIENT_SMEM_ARCS * (int)sizeof(int))
+
 #define GS_LOOP(i, n) \
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)(n); \
          i += (long long)gridDim.x * blockDim.x)
@@ -463,6 +467,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
             a.bsum[i] = pre;
             pre += (int)t;
         }
+        if (threadIdx.x == 0) ctl->ncore = (u64)tot;   // core arcs = slots of the core adjacency
     }
     if (!grid_barrier(ctl, &ctl->bar[2])) return;
     {
@@ -495,7 +500,10 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         a.apos[i] = slot;
     }
     if (!grid_barrier(ctl, &ctl->bar[2])) return;
-    // phase 5: Euler successors of core arcs; open the circuit at each root
+    // phase 5: Euler successors of core arcs, in slot space (the position of
+    // an arc in the core adjacency array): the successor of arc a->b is the
+    // slot after b->a's slot in b's list, wrapping to the list start; the
+    // circuit is opened at each super-tree root
     for (long long i = gtid(); i < 2 * ner; i += gstride()) {
         if (LD(a.lf[i >> 1])) continue;
         long long tw = i ^ 1;
@@ -507,42 +515,81 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         int succ;
         if (nx == end) {
             bool is_root = LD(a.minp[find_root(a.comp, head, ctl)]) == head;
-            succ = is_root ? NIL : LD(a.adj[start]);
+            succ = is_root ? NIL : start;
         } else {
-            succ = LD(a.adj[nx]);
+            succ = nx;
         }
-        a.nx0[i] = succ;
-        a.val0[i] = 1;
+        int si = LD(a.apos[i]);
+        a.nx0[si] = succ;
+        a.val0[si] = 1;
     }
     if (!grid_barrier(ctl, &ctl->bar[2])) return;
-    // phase 6: list ranking (Wyllie): val = arcs from here to the tour end
+    // phase 6: list ranking (Wyllie): val = arcs from here to the tour end.
+    // A core of at most ORIENT_SMEM_ARCS arcs is ranked by block 0 alone in
+    // shared memory (block barriers instead of grid barriers per round).
+    const long long ncore = (long long)*(volatile u64 *)&ctl->ncore;
     int *vc = a.val0, *vn = a.val1, *nc = a.nx0, *nn = a.nx1;
     int r = 0;
-    for (;; ++r) {
-        if (r >= MAX_ROUNDS) {
-            if (gtid() == 0) atomicOr(&ctl->err, ERR_ROUNDS);
-            return;
-        }
-        if (gtid() == 0) ctl->flag[(r + 1) % 3] = 0;
-        bool ch = false;
-        for (long long i = gtid(); i < 2 * ner; i += gstride()) {
-            if (LD(a.lf[i >> 1])) continue;
-            int s = LD(nc[i]);
-            if (s != NIL) {
-                vn[i] = LD(vc[i]) + LD(vc[s]);
-                nn[i] = LD(nc[s]);
-                ch = true;
-            } else {
-                vn[i] = LD(vc[i]);
-                nn[i] = NIL;
+    if (ncore <= ORIENT_SMEM_ARCS) {
+        if (blockIdx.x == 0) {
+            extern __shared__ int s_rank[];
+            int *svc = s_rank, *svn = svc + ORIENT_SMEM_ARCS, *snc = svn + ORIENT_SMEM_ARCS,
+                *snn = snc + ORIENT_SMEM_ARCS;
+            for (long long i = threadIdx.x; i < ncore; i += blockDim.x) {
+                svc[i] = LD(a.val0[i]);
+                snc[i] = LD(a.nx0[i]);
             }
+            __syncthreads();
+            for (;; ++r) {
+                int ch = 0;
+                for (long long i = threadIdx.x; i < ncore; i += blockDim.x) {
+                    int sx = snc[i];
+                    if (sx != NIL) {
+                        svn[i] = svc[i] + svc[sx];
+                        snn[i] = snc[sx];
+                        ch = 1;
+                    } else {
+                        svn[i] = svc[i];
+                        snn[i] = NIL;
+                    }
+                }
+                int any = __syncthreads_or(ch);
+                int *t = svc; svc = svn; svn = t;
+                t = snc; snc = snn; snn = t;
+                if (!any || r >= MAX_ROUNDS) break;
+            }
+            for (long long i = threadIdx.x; i < ncore; i += blockDim.x) a.val0[i] = svc[i];
+            if (threadIdx.x == 0) ctl->rank_rounds = r + 1;
         }
-        if (__syncthreads_or(ch) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
         if (!grid_barrier(ctl, &ctl->bar[2])) return;
-        int again = *(volatile int *)&ctl->flag[r % 3];
-        int *t = vc; vc = vn; vn = t;
-        t = nc; nc = nn; nn = t;
-        if (!again) break;
+        vc = a.val0;
+    } else {
+        for (;; ++r) {
+            if (r >= MAX_ROUNDS) {
+                if (gtid() == 0) atomicOr(&ctl->err, ERR_ROUNDS);
+                return;
+            }
+            if (gtid() == 0) ctl->flag[(r + 1) % 3] = 0;
+            bool ch = false;
+            for (long long i = gtid(); i < ncore; i += gstride()) {
+                int sx = LD(nc[i]);
+                if (sx != NIL) {
+                    vn[i] = LD(vc[i]) + LD(vc[sx]);
+                    nn[i] = LD(nc[sx]);
+                    ch = true;
+                } else {
+                    vn[i] = LD(vc[i]);
+                    nn[i] = NIL;
+                }
+            }
+            if (__syncthreads_or(ch) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
+            if (!grid_barrier(ctl, &ctl->bar[2])) return;
+            int again = *(volatile int *)&ctl->flag[r % 3];
+            int *t = vc; vc = vn; vn = t;
+            t = nc; nc = nn; nn = t;
+            if (!again) break;
+        }
+        if (gtid() == 0) ctl->rank_rounds = r + 1;
     }
     // phase 7: orient, attach points, new roots
     for (long long i = gtid(); i < ner; i += gstride()) {
@@ -552,7 +599,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         unsigned char lf = LD(a.lf[i]);
         bool down;                                 // true: p0 is the parent of p1
         if (lf) down = lf == 2;
-        else down = LD(vc[2 * i]) > LD(vc[2 * i + 1]);
+        else down = LD(vc[LD(a.apos[2 * i])]) > LD(vc[LD(a.apos[2 * i + 1])]);
         int child = down ? p1 : p0;
         int x = down ? x1 : x0, y = down ? x0 : x1;
         a.chx[i] = x;
@@ -565,7 +612,6 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         a.rep_ep[p0] = ep;
         a.rep_ep[p1] = ep;
     }
-    if (gtid() == 0) ctl->rank_rounds = r + 1;
 }
 
 // Path-reversal set-up fused with the representative refresh: a vertex of a
@@ -696,7 +742,15 @@ static unsigned coop_blocks(const void *fn, int nsm, int cap_per_sm) {
 }
 unsigned coop_blocks_jump(int nsm) { return coop_blocks((const void *)k_jump, nsm, 8); }
 unsigned coop_blocks_hook(int nsm) { return coop_blocks((const void *)k_boruvka, nsm, 4); }
-unsigned coop_blocks_orient(int nsm) { return coop_blocks((const void *)k_orient, nsm, 2); }
+unsigned coop_blocks_orient(int nsm) {
+    cudaFuncSetAttribute((const void *)k_orient, cudaFuncAttributeMaxDynamicSharedMemorySize, ORIENT_SMEM_BYTES);
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k_orient, BLK, ORIENT_SMEM_BYTES) !=
+            cudaSuccess || per < 1)
+        per = 1;
+    if (per > 2) per = 2;
+    return (unsigned)(per * nsm);
+}
 unsigned coop_blocks_mark(int nsm) { return coop_blocks((const void *)k_mark, nsm, 4); }
 
 cudaError_t launch_begin(Ctl *ctl, int op, long long len, cudaStream_t s) {
@@ -729,7 +783,7 @@ cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0,
 }
 cudaError_t launch_orient(const Dev &d, Ctl *ctl, OrientArgs a, cudaStream_t s) {
     void *args[] = {(void *)&ctl, (void *)&a};
-    return cudaLaunchCooperativeKernel((const void *)k_orient, d.coop_orient, BLK, args, 0, s);
+    return cudaLaunchCooperativeKernel((const void *)k_orient, d.coop_orient, BLK, args, ORIENT_SMEM_BYTES, s);
 }
 cudaError_t launch_active(const Dev &d, const int *L, int use_list, long long cnt_static, Ctl *ctl, int *rep,
                           const int *parent, const unsigned *att_ep, const int *att_x, const unsigned *rep_ep,

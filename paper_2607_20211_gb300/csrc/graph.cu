@@ -351,15 +351,21 @@ __global__ void k_scan_lb(const int *D, const long long *roff, Ctl *ctl, Csr g, 
     r0 = __shfl_sync(0xffffffffu, r0, 0);
     for (long long t0 = e_lo; t0 < e_hi; t0 += 32) {
         const long long e = t0 + lane;
+        // rows r0 .. r0+31 start at wv; the rows after r0 that start inside
+        // this tile set a bit at their start position, and the row of
+        // position q is r0 plus the number of such starts at positions <= q
         const long long wv = r0 + lane < nd ? roff[r0 + lane] : LLONG_MAX;
-        int c = 0;
-        for (int k = 0; k < 32; ++k) c += __shfl_sync(0xffffffffu, wv, k) <= e;
-        const long long r = r0 + c - 1;
+        const long long pos = wv - t0;
+        const unsigned bit = (lane > 0 && pos >= 0 && pos < 32) ? (1u << pos) : 0u;
+        const unsigned starts = __reduce_or_sync(0xffffffffu, bit);
+        const int c = __popc(starts & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u)));
+        const long long r = r0 + c;
+        const long long rstart = __shfl_sync(0xffffffffu, wv, c);   // all lanes take part
         bool emit = false;
         int u = 0, x = -1, ru = 0, rx = 0;
         if (e < e_hi) {
             u = D[r];
-            long long j = e - __shfl_sync(0xffffffffu, wv, c - 1);
+            long long j = e - rstart;
             x = __ldcs(&g.col[g.off[u] + j]);
             if (x >= 0) {
                 ru = rep[u];
