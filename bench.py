@@ -186,7 +186,7 @@ def phase_bytes(st: dict, n: int, op: int) -> dict:
         aff, det, sc, c = st["affected"], st["detached"], st["scanned"], st["candidates"]
         out["del_claim"] = 8 * b + 40 * a + 12 * st["tree_cut"]
         out["affected"] = 8 * n + 12 * aff
-        out["jump"] = 16 * aff * max(st["jump_rounds"], 1) + 76 * aff + 4 * det
+        out["jump"] = 16 * st.get("jump_visits", aff * max(st["jump_rounds"], 1)) + 64 * aff + 4 * det
         out["scan"] = 40 * det + 8 * sc + 32 * c
         out["active"] = 16 * aff + 16 * st["active"]
     c, ner = st["candidates"], st["replacement"]
@@ -326,7 +326,7 @@ def run_ours(args, rank, ws, local):
         return round(float(np.mean([steps[W + k][op][1][key] for k in range(K)])), 1)
     batch_stats = {oname: {key: _mean(op, key) for key in (
         "applied", "tree_cut", "affected", "detached", "scanned", "candidates", "hook_rounds", "replacement",
-        "rank_rounds", "active", "reversed", "mark_rounds", "jump_rounds")} for op, oname in ((0, "insert"),
+        "rank_rounds", "active", "reversed", "mark_rounds", "jump_rounds", "jump_visits")} for op, oname in ((0, "insert"),
                                                                                         (1, "delete"))}
 
     # end to end through the C ABI with host buffers

@@ -108,6 +108,7 @@ typedef struct {
     int64_t edges;         /* |E(G')| after the batch */
     int64_t overflow;      /* edges held outside their CSR row (slack exhausted) */
     int64_t rebuilds;      /* CSR / index rebuilds so far */
+    int64_t jump_visits;   /* vertex visits summed over the pointer-jumping rounds */
 } drsf_batch_stats;
 
 /* Allocator hooks.  alloc(bytes, stream, ctx) returns device memory or NULL;

@@ -54,7 +54,7 @@ struct drsf_ctx {
     int *chx = nullptr, *chy = nullptr;
     unsigned *aff_ep = nullptr, *cut_ep = nullptr, *pstamp = nullptr, *att_ep = nullptr, *rep_ep = nullptr;
     u64 *best0 = nullptr, *best1 = nullptr, *er = nullptr, *heavy = nullptr;
-    int *rold = nullptr, *cdeg = nullptr;
+    int *rold = nullptr, *cdeg = nullptr, *xlist = nullptr;
     long long *roff = nullptr;
     unsigned char *lf = nullptr;
     unsigned *wgt = nullptr;
@@ -422,6 +422,7 @@ static drsf_status alloc_work(drsf_ctx *h, cudaStream_t s) {
     CKA(halloc(h, &h->heavy, n, s));
     CKA(halloc(h, &h->rold, n, s));
     CKA(halloc(h, &h->roff, n + 1, s));
+    CKA(halloc(h, &h->xlist, n, s));
     CKA(halloc(h, &h->cdeg, n + 1, s));
     CKA(halloc(h, &h->lf, n + 1, s));
     CKA(halloc(h, &h->wgt, n, s));
@@ -492,7 +493,7 @@ static drsf_status create_impl(drsf_ctx *h, const int32_t *edges, int64_t m, con
     CK(launch_copy_parent(n, h->parent, h->J0, s));
     Csr g0{h->off, h->used, h->col};
     CK(launch_jump(h->dev, nullptr, 0, n, h->ctl, h->J0, h->J1, h->rep, h->D, 0, h->rold, h->wgt, h->heavy, g0,
-                   h->roff, h->bsum, h->jump_sync, s));
+                   h->roff, h->bsum, h->jump_sync, h->act, h->xlist, s));
     Ctl c{};
     CK(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -604,7 +605,7 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
         prof_end(h, PH_AFF, 1, s);
         prof_begin(h, PH_JUMP, s);
         CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->J0, h->J1, h->rep, h->D, 1, h->rold, h->wgt, h->heavy, g,
-                       h->roff, h->bsum, h->jump_sync, s));
+                       h->roff, h->bsum, h->jump_sync, h->act, h->xlist, s));
         prof_end(h, PH_JUMP, 1, s);
         prof_begin(h, PH_SCAN, s);
         CK(launch_scan_rows(h->dev, h->D, h->roff, ctl, g, h->rep, h->rold, h->heavy, h->pt, h->ck[0], h->ca[0],
@@ -766,6 +767,7 @@ drsf_status drsf_stats(drsf_handle h, drsf_batch_stats *out, drsf_stream stream)
     out->edges = c.edges;
     out->overflow = (int64_t)c.ovf_count;
     out->rebuilds = h->rebuilds;
+    out->jump_visits = c.jump_visits;
     return latched(h);
 }
 

@@ -67,6 +67,7 @@ struct Ctl {
     long long rank_rounds;
     long long mark_rounds;
     long long jump_rounds;
+    long long jump_visits;
     long long reversed;
     long long batch_len;
     long long overflow_total;

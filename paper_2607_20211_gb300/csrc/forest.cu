@@ -37,6 +37,7 @@ __global__ void k_begin(Ctl *ctl, int op, long long len) {
     ctl->nb = ctl->ncut = ctl->naff = ctl->ndet = ctl->ncand = ctl->ner = ctl->npc = ctl->nact = 0;
     ctl->scanned = ctl->self_loops = ctl->dropped = ctl->tree_cut = 0;
     ctl->hook_rounds = ctl->rank_rounds = ctl->mark_rounds = ctl->jump_rounds = ctl->reversed = 0;
+    ctl->jump_visits = 0;
     ctl->batch_len = len;
     for (int i = 0; i < 3; ++i) {
         ctl->flag[i] = 0;
@@ -98,7 +99,7 @@ __device__ __forceinline__ int find_halving(int *J, int v, Ctl *ctl) {
 // their lengths in roff (roff[ndet] = total) for the load-balanced scan.
 __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1, int *rep,
                        int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g, long long *roff,
-                       long long *bsum, int sync_rounds) {
+                       long long *bsum, int sync_rounds, int *X, int *Y) {
     if (*(volatile int *)&ctl->skip) return;
     long long cnt = use_list ? (long long)ctl->naff : cnt_static;
     if (sync_rounds) {
@@ -106,39 +107,59 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
         // reached a root is stored complemented (negative): a converged
         // vertex skips the gather, and the loop ends in the first round in
         // which every listed vertex is converged (no verification round).
+        // Round r reads the list of vertices still open (the full list in
+        // round 0) and appends the ones still open after it to the other
+        // work list (X, Y alternate); a vertex that converges writes its
+        // complemented root into both buffers, so later reads of it from
+        // either buffer see the root.
         int *Jc = J, *Jn = J1;
         int r = 0;
+        if (gtid() == 0) {
+            ctl->cnt[0] = (u64)cnt;
+            ctl->cnt[1] = 0;
+        }
+        if (!grid_barrier(ctl, &ctl->bar[0])) return;
         for (;; ++r) {
             if (r >= MAX_ROUNDS) {
                 if (gtid() == 0) atomicOr(&ctl->err, ERR_ROUNDS);
                 return;
             }
-            if (gtid() == 0) ctl->flag[(r + 1) % 3] = 0;
-            bool open = false;
-            for (long long i = gtid(); i < cnt; i += gstride()) {
-                int v = use_list ? A[i] : (int)i;
-                int w0 = LD(Jc[v]);
-                int nv;
-                if (w0 < 0) {
-                    nv = w0;
-                } else {
-                    int w2 = LD(Jc[w0]);
-                    if (w2 < 0) nv = w2;
-                    else if (w2 == w0) nv = ~w0;
-                    else {
-                        nv = w2;
-                        open = true;
-                    }
-                }
-                Jn[v] = nv;
+            const long long c = (long long)*(volatile u64 *)&ctl->cnt[r % 3];
+            if (c == 0) break;
+            if (gtid() == 0) {
+                ctl->cnt[(r + 2) % 3] = 0;
+                ctl->jump_visits += c;
             }
-            if (__syncthreads_or(open) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
+            const int *in = r == 0 ? (use_list ? A : nullptr) : ((r & 1) ? X : Y);
+            int *out = (r & 1) ? Y : X;
+            for (long long base = (long long)blockIdx.x * blockDim.x; base < c; base += gstride()) {
+                long long i = base + threadIdx.x;
+                bool open = false;
+                int v = 0, nv = 0;
+                if (i < c) {
+                    v = in ? in[i] : (int)i;
+                    int w0 = LD(Jc[v]);
+                    if (w0 < 0) {
+                        nv = w0;
+                    } else {
+                        int w2 = LD(Jc[w0]);
+                        if (w2 < 0) nv = w2;
+                        else if (w2 == w0) nv = ~w0;
+                        else {
+                            nv = w2;
+                            open = true;
+                        }
+                    }
+                    Jn[v] = nv;
+                    if (!open) Jc[v] = nv;
+                }
+                long long q = block_append(&ctl->cnt[(r + 1) % 3], open);
+                if (open) out[q] = v;
+            }
             if (!grid_barrier(ctl, &ctl->bar[0])) return;
-            int again = *(volatile int *)&ctl->flag[r % 3];
             int *t = Jc; Jc = Jn; Jn = t;
-            if (!again) break;
         }
-        if (gtid() == 0) ctl->jump_rounds = r + 1;
+        if (gtid() == 0) ctl->jump_rounds = r;
         if (mode == 0) {
             for (long long i = gtid(); i < cnt; i += gstride()) {
                 int v = use_list ? A[i] : (int)i;
@@ -397,8 +418,9 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         int p = a.rep[(i & 1) ? khi(k) : klo(k)];
         int root = find_root(a.comp, p, ctl);
         a.minp[root] = INT_MAX;
-        if (atomicExch(&a.pstamp[p], ep) != ep) {
-            long long id = (long long)atomicAdd(&ctl->npc, 1ull);
+        bool first = atomicExch(&a.pstamp[p], ep) != ep;
+        long long id = agg_append(&ctl->npc, first);
+        if (first) {
             a.pidx[p] = (int)id;
             a.plist[id] = p;
             a.pdeg[id] = 0;
@@ -769,10 +791,10 @@ cudaError_t launch_copy_parent(int n, const int *parent, int *J0, cudaStream_t s
 }
 cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1,
                         int *rep, int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g,
-                        long long *roff, long long *bsum, int sync_rounds, cudaStream_t s) {
+                        long long *roff, long long *bsum, int sync_rounds, int *X, int *Y, cudaStream_t s) {
     void *args[] = {(void *)&A, (void *)&use_list, (void *)&cnt_static, (void *)&ctl, (void *)&J, (void *)&J1,
                     (void *)&rep, (void *)&D, (void *)&mode, (void *)&rold, (void *)&w, (void *)&heavy,
-                    (void *)&g, (void *)&roff, (void *)&bsum, (void *)&sync_rounds};
+                    (void *)&g, (void *)&roff, (void *)&bsum, (void *)&sync_rounds, (void *)&X, (void *)&Y};
     return cudaLaunchCooperativeKernel((const void *)k_jump, d.coop_jump, BLK, args, 0, s);
 }
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
