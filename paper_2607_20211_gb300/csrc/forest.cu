@@ -298,10 +298,19 @@ __global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int 
     long long c0 = (long long)ctl->ncand;
     for (long long i = gtid(); i < c0; i += gstride()) {
         int a = ca0[i], b = cb0[i];
-        comp[a] = a;
-        comp[b] = b;
-        best0[a] = best0[b] = EMPTY_KEY;
-        best1[a] = best1[b] = EMPTY_KEY;
+        // one lane per distinct piece writes (a piece such as the giant one
+        // can be an endpoint of most candidates)
+        unsigned act = __activemask();
+        unsigned ga = __match_any_sync(act, a), gb = __match_any_sync(act, b);
+        int lane = threadIdx.x & 31;
+        if (lane == __ffs(ga) - 1) {
+            comp[a] = a;
+            best0[a] = best1[a] = EMPTY_KEY;
+        }
+        if (lane == __ffs(gb) - 1) {
+            comp[b] = b;
+            best0[b] = best1[b] = EMPTY_KEY;
+        }
     }
     if (gtid() == 0) {
         ctl->cnt[0] = (u64)c0;
@@ -416,8 +425,6 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
     for (long long i = gtid(); i < 2 * ner; i += gstride()) {
         u64 k = a.er[i >> 1];
         int p = a.rep[(i & 1) ? khi(k) : klo(k)];
-        int root = find_root(a.comp, p, ctl);
-        a.minp[root] = INT_MAX;
         bool first = atomicExch(&a.pstamp[p], ep) != ep;
         long long id = agg_append(&ctl->npc, first);
         if (first) {
@@ -426,6 +433,9 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
             a.pdeg[id] = 0;
             a.cdeg[id] = 0;
             a.pcur[id] = 0;
+            // the root piece of the hook forest holds its super-tree's slot;
+            // one write per super-tree (many threads share one root)
+            if (find_root(a.comp, p, ctl) == p) a.minp[p] = INT_MAX;
         }
     }
     if (!grid_barrier(ctl, &ctl->bar[2])) return;
@@ -626,13 +636,12 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         int x = down ? x1 : x0, y = down ? x0 : x1;
         a.chx[i] = x;
         a.chy[i] = y;
+        // each non-root piece is the child of exactly one edge: one write
+        // per piece; the super-root keeps its representative
         a.att_x[child] = x;
         a.att_ep[child] = ep;
-        int nr0 = LD(a.minp[find_root(a.comp, p0, ctl)]);
-        a.newrep[p0] = nr0;
-        a.newrep[p1] = nr0;
-        a.rep_ep[p0] = ep;
-        a.rep_ep[p1] = ep;
+        a.newrep[child] = LD(a.minp[find_root(a.comp, p0, ctl)]);
+        a.rep_ep[child] = ep;
     }
 }
 

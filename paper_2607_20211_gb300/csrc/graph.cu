@@ -296,9 +296,18 @@ __global__ void k_del_claim(const int *batch, long long len, Index ix, Csr g, u6
                 if (c >= 0) {
                     parent[c] = c;
                     cut_ep[c] = ep;
-                    aff_ep[rep[c]] = ep;
                     w[c] = 0;   // c roots a new piece: its weight slot
                 }
+            }
+        }
+        {
+            // stamp the cut trees' old roots; lanes cutting the same tree
+            // write once (most cuts can fall in one giant tree)
+            int r = c >= 0 ? rep[c] : -1;
+            unsigned m = __ballot_sync(__activemask(), c >= 0);
+            if (c >= 0) {
+                unsigned grp = __match_any_sync(m, r);
+                if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) aff_ep[r] = ep;
             }
         }
         agg_count(&ctl->self_loops, u == v);
