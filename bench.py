@@ -276,6 +276,17 @@ def run_ours(args, rank, ws, local):
     barrier()
     prof = f.profile_stop()
     final = f.parent().cpu().numpy()
+    # static rebuild of the final graph from scratch (the plain alternative)
+    st_ms = []
+    levels = 0
+    for rep_i in range(5):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, levels = f.static_forest(with_levels=True) if rep_i == 0 else (*f.static_forest(), levels)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st_ms.append(e0.elapsed_time(e1))
     f.close()
     if not np.array_equal(final, final_plan):
         raise RuntimeError("timed replay diverged from the planning pass")
@@ -374,6 +385,11 @@ def run_ours(args, rank, ws, local):
                              "p99": round(float(np.percentile(lat, 99)), 4),
                              "insert_p50": round(float(np.median(ins_ms)), 4),
                              "delete_p50": round(float(np.median(del_ms)), 4)},
+        "static_rebuild": {"ms": round(float(np.median(st_ms[1:])), 4), "bfs_levels": int(levels),
+                           "what": "components by hook-and-compress + multi-source BFS from component minima, "
+                                   "on the final graph, same GPU",
+                           "x_insert_batch": round(float(np.median(st_ms[1:])) / float(np.median(ins_ms)), 2),
+                           "x_delete_batch": round(float(np.median(st_ms[1:])) / float(np.median(del_ms)), 2)},
         "roofline": roofline, "phases": phase_table, "batch_stats": batch_stats, "e2e": e2e,
         "cpu_baseline": cpu,
         "gpu_launches": int(sum(v[1] for v in phases.values())),

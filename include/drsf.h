@@ -190,6 +190,24 @@ DRSF_API int64_t drsf_num_edges(drsf_handle h, drsf_stream stream);
 DRSF_API drsf_status drsf_export_edges(drsf_handle h, int32_t *out, int64_t cap, int64_t *m_out, drsf_stream stream);
 
 /*
+ * drsf_static_forest -- a rooted spanning forest of the handle's current
+ * graph built from scratch, the static alternative the paper compares the
+ * dynamic update with (Section V-B: connected components by hooking and
+ * shortcutting, the component representatives, then parallel BFS from
+ * them).  Components by hook-and-compress over every edge (larger root
+ * under smaller, so each root is its component's smallest vertex), then a
+ * level-synchronous multi-source BFS from those roots.
+ *   parent_out  device int32[n]: a BFS forest (parent[r] == r at the
+ *               component minima); which neighbour becomes a vertex's
+ *               parent depends on thread timing, the roots do not
+ *   labels_out  device int32[n] or NULL: smallest vertex id per component
+ *   levels_out  host or NULL: BFS levels (synchronises when given)
+ * Does not change the handle's forest.  Enqueued on `stream`.
+ */
+DRSF_API drsf_status drsf_static_forest(drsf_handle h, int32_t *parent_out, int32_t *labels_out,
+                                        int64_t *levels_out, drsf_stream stream);
+
+/*
  * Per-phase timing (instrumentation; not part of the paper).  Between
  * drsf_profile_start and drsf_profile_stop every drsf_apply brackets each
  * phase of the update with CUDA events on its stream; stop synchronises and

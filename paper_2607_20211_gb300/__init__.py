@@ -129,6 +129,8 @@ def _load():
         lib.drsf_profile_start.argtypes = [vp, i64]
         lib.drsf_profile_stop.restype = ctypes.c_int
         lib.drsf_profile_stop.argtypes = [vp, P(Profile), vp]
+        lib.drsf_static_forest.restype = ctypes.c_int
+        lib.drsf_static_forest.argtypes = [vp, vp, vp, P(i64), vp]
         lib.drsf_selftest_barrier_timeout.restype = ctypes.c_int
         lib.drsf_selftest_barrier_timeout.argtypes = [vp]
         lib.drsf_phase_name.restype = ctypes.c_char_p
@@ -268,6 +270,19 @@ class DynamicForest:
         if st:
             raise DRSFError(st, "drsf_export_edges")
         return out[:got.value]
+
+    def static_forest(self, with_levels: bool = False):
+        """A rooted spanning forest of the current graph rebuilt from scratch
+        (components + multi-source BFS from their minima); returns
+        (parent, labels[, levels]) as device tensors."""
+        par = torch.empty(self._n, dtype=torch.int32, device="cuda")
+        lab = torch.empty(self._n, dtype=torch.int32, device="cuda")
+        lv = ctypes.c_int64(0)
+        st = _lib.drsf_static_forest(self._h, par.data_ptr(), lab.data_ptr(),
+                                     ctypes.byref(lv) if with_levels else None, _stream_ptr(self._stream))
+        if st:
+            raise DRSFError(st, "drsf_static_forest")
+        return (par, lab, lv.value) if with_levels else (par, lab)
 
     def profile_start(self, max_batches: int) -> None:
         """Start per-phase CUDA-event timing of the next batches."""

@@ -556,6 +556,7 @@ drsf_status drsf_create(int32_t n, const int32_t *edges, int64_t m, const int32_
     h->dev.coop_hook = coop_blocks_hook(nsm);
     h->dev.coop_orient = coop_blocks_orient(nsm);
     h->dev.coop_mark = coop_blocks_mark(nsm);
+    h->dev.coop_bfs = coop_blocks_bfs(nsm);
     // DRSF_JUMP=halving selects the in-place path-halving root search
     const char *jm = getenv("DRSF_JUMP");
     h->jump_sync = (jm && strcmp(jm, "halving") == 0) ? 0 : 1;
@@ -836,6 +837,25 @@ drsf_status drsf_profile_stop(drsf_handle h, drsf_profile_t *out, drsf_stream st
 
 const char *drsf_phase_name(int phase) {
     return phase >= 0 && phase < DRSF_NUM_PHASES ? kPhaseNames[phase] : "?";
+}
+
+drsf_status drsf_static_forest(drsf_handle h, int32_t *parent_out, int32_t *labels_out, int64_t *levels_out,
+                               drsf_stream stream) {
+    if (!h || !parent_out) return DRSF_EINVAL;
+    if (h->poisoned) return DRSF_EPOISONED;
+    set_dev(h);
+    cudaStream_t s = (cudaStream_t)stream;
+    int *lab = labels_out ? labels_out : h->J1;
+    u64 *levels = (u64 *)h->bsum;   // scratch word
+    Csr g{h->off, h->used, h->col};
+    CK(launch_static_forest(h->dev, h->n, g, h->ovf, h->ctl, lab, parent_out, h->act, h->xlist, levels, s));
+    if (levels_out) {
+        long long lv = 0;
+        CK(cudaMemcpyAsync(&lv, levels, sizeof lv, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        *levels_out = lv;
+    }
+    return DRSF_OK;
 }
 
 drsf_status drsf_selftest_barrier_timeout(drsf_stream stream) {

@@ -14,6 +14,7 @@ struct Dev {
     unsigned coop_hook;
     unsigned coop_orient;
     unsigned coop_mark;
+    unsigned coop_bfs;
 };
 
 // graph.cu -------------------------------------------------------------
@@ -89,3 +90,7 @@ unsigned coop_blocks_hook(int nsm);
 unsigned coop_blocks_orient(int nsm);
 unsigned coop_blocks_mark(int nsm);
 cudaError_t launch_barrier_selftest(Ctl *ctl, cudaStream_t s);
+// static.cu ------------------------------------------------------------
+cudaError_t launch_static_forest(const Dev &d, int n, Csr g, const u64 *ovf, Ctl *ctl, int *lab, int *parent,
+                                 int *f0, int *f1, u64 *levels, cudaStream_t s);
+unsigned coop_blocks_bfs(int nsm);
