@@ -845,10 +845,11 @@ drsf_status drsf_static_forest(drsf_handle h, int32_t *parent_out, int32_t *labe
     if (h->poisoned) return DRSF_EPOISONED;
     set_dev(h);
     cudaStream_t s = (cudaStream_t)stream;
-    int *lab = labels_out ? labels_out : h->J1;
+    int *comp = labels_out ? labels_out : h->pold;
     u64 *levels = (u64 *)h->bsum;   // scratch word
     Csr g{h->off, h->used, h->col};
-    CK(launch_static_forest(h->dev, h->n, g, h->ovf, h->ctl, lab, parent_out, h->act, h->xlist, levels, s));
+    CK(launch_static_forest(h->dev, h->n, g, h->ovf, h->ctl, h->J1, comp, parent_out, h->act, h->xlist, levels,
+                            s));
     if (levels_out) {
         long long lv = 0;
         CK(cudaMemcpyAsync(&lv, levels, sizeof lv, cudaMemcpyDeviceToHost, s));

@@ -91,6 +91,6 @@ unsigned coop_blocks_orient(int nsm);
 unsigned coop_blocks_mark(int nsm);
 cudaError_t launch_barrier_selftest(Ctl *ctl, cudaStream_t s);
 // static.cu ------------------------------------------------------------
-cudaError_t launch_static_forest(const Dev &d, int n, Csr g, const u64 *ovf, Ctl *ctl, int *lab, int *parent,
-                                 int *f0, int *f1, u64 *levels, cudaStream_t s);
+cudaError_t launch_static_forest(const Dev &d, int n, Csr g, const u64 *ovf, Ctl *ctl, int *lab, int *comp,
+                                 int *parent, int *f0, int *f1, u64 *levels, cudaStream_t s);
 unsigned coop_blocks_bfs(int nsm);

@@ -64,15 +64,22 @@ __global__ void k_cc_hook(int n, Csr g, const u64 *ovf, const Ctl *ctl, int *lab
     }
 }
 
-// Compress to roots; roots start the BFS (parent[r] = r), other vertices
-// are unclaimed (-1).
-__global__ void k_cc_roots(int n, int *lab, int *parent, int *frontier, u64 *fcount) {
+// Component of every vertex by a read-only walk to its root, written to a
+// separate array (a walk that rewrote the pointers it reads could race with
+// another walk and leave a non-root behind); roots start the BFS
+// (parent[r] = r), other vertices are unclaimed (-1).
+__global__ void k_cc_roots(int n, const int *lab, int *comp, int *parent, int *frontier, u64 *fcount) {
     for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
         long long v = base + threadIdx.x;
         bool root = false;
         if (v < n) {
-            int r = cc_find(lab, (int)v);
-            lab[v] = r;
+            int r = (int)v;
+            for (int it = 0; it < (1 << 22); ++it) {
+                int p = __ldcg(&lab[r]);
+                if (p == r) break;
+                r = p;
+            }
+            comp[v] = r;
             root = r == (int)v;
             parent[v] = root ? (int)v : -1;
         }
@@ -141,14 +148,14 @@ unsigned coop_blocks_bfs(int nsm) {
     return (unsigned)(per * nsm);
 }
 
-cudaError_t launch_static_forest(const Dev &d, int n, Csr g, const u64 *ovf, Ctl *ctl, int *lab, int *parent,
-                                 int *f0, int *f1, u64 *levels, cudaStream_t s) {
+cudaError_t launch_static_forest(const Dev &d, int n, Csr g, const u64 *ovf, Ctl *ctl, int *lab, int *comp,
+                                 int *parent, int *f0, int *f1, u64 *levels, cudaStream_t s) {
     unsigned gn = grid_for(n, BLK, 152u * 16u);
     cudaError_t e = cudaMemsetAsync(ctl->cnt, 0, sizeof(ctl->cnt), s);
     if (e != cudaSuccess) return e;
     k_cc_init<<<gn, BLK, 0, s>>>(n, lab);
     k_cc_hook<<<d.grid, BLK, 0, s>>>(n, g, ovf, ctl, lab);
-    k_cc_roots<<<gn, BLK, 0, s>>>(n, lab, parent, f0, &ctl->cnt[0]);
+    k_cc_roots<<<gn, BLK, 0, s>>>(n, lab, comp, parent, f0, &ctl->cnt[0]);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&ctl, (void *)&g, (void *)&ovf, (void *)&parent, (void *)&f0, (void *)&f1,
