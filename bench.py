@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="rmat22",
-                   choices=["rmat22", "rmat20", "grid4096", "er-small"])
+                   choices=["rmat22", "rmat20", "grid4096", "er-small", "batched256"])
     p.add_argument("--batch", type=int, default=0, help="batch size (default per workload)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -398,6 +398,99 @@ def run_ours(args, rank, ws, local):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, rank, ws, local):
+    """256 independent graphs (n log-uniform in [1K, 256K], half Erdos-Renyi,
+    half R-MAT, average degree uniform in [4, 16], seed 4); each step gives
+    every graph an insert batch then a delete batch (together 1-10% of its
+    m, 60/40, deletes 50% tree edges).  Batched form: one launch sequence
+    over the disjoint union of the graphs (ids offset per graph); compared
+    with one launch sequence per graph (256 handles) on the same GPU."""
+    import torch
+    import paper_2607_20211_gb300 as drsf
+    import workloads
+    torch.cuda.set_device(local)
+    drsf.build()
+    K, W = args.steps, args.warmup
+    graphs = workloads.batched_graphs(256, seed=4)
+    U = workloads.Union(graphs)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
+    edges_u, par_u = dev(workloads.keys_to_edges(U.keys)), dev(U.parent)
+    # planning pass on the union handle: per-graph batches from per-graph state
+    f = drsf.DynamicForest(U.n, edges_u, par_u)
+    trs = [workloads.Trajectory(g, seed=(4 << 20) + i) for i, g in enumerate(graphs)]
+    plan_steps = []
+    for s in range(W + K):
+        budgets = workloads.batched_budgets(graphs, seed=4 + 7919 * s)
+        pair = []
+        for op in (0, 1):
+            per = [tr.next_batch(op, b[op]) for tr, b in zip(trs, budgets)]
+            f.apply(op, dev(np.concatenate([U.shift(i, b) for i, b in enumerate(per)])))
+            parts = U.split(f.parent().cpu().numpy())
+            for tr, b, p in zip(trs, per, parts):
+                tr.advance(b, op, p)
+            pair.append(per)
+        plan_steps.append(pair)
+    final_plan = f.parent().cpu().numpy()
+    f.close()
+    ubat = [[dev(np.concatenate([U.shift(i, b) for i, b in enumerate(pair[op])])) for op in (0, 1)]
+            for pair in plan_steps]
+    gbat = [[[dev(b) for b in pair[op]] for op in (0, 1)] for pair in plan_steps]
+    updates = sum(sum(len(b) for b in pair[op]) for pair in plan_steps[W:] for op in (0, 1))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(apply_step):
+        tot = 0.0
+        for k in range(W + K):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            apply_step(k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= W:
+                tot += e0.elapsed_time(e1)
+        return tot / 1e3
+
+    f = drsf.DynamicForest(U.n, edges_u, par_u)
+    barrier()
+    t_union = timed(lambda k: (f.apply(0, ubat[k][0]), f.apply(1, ubat[k][1])))
+    final = f.parent().cpu().numpy()
+    f.close()
+    if not np.array_equal(final, final_plan):
+        raise RuntimeError("batched replay diverged from the planning pass")
+    hs = [drsf.DynamicForest(g.n, dev(g.edges()), dev(g.parent)) for g in graphs]
+
+    def per_graph(k):
+        for op in (0, 1):
+            for h, b in zip(hs, gbat[k][op]):
+                h.apply(op, b)
+    t_each = timed(per_graph)
+    parts = [h.parent().cpu().numpy() for h in hs]
+    for h in hs:
+        h.close()
+    same = all(np.array_equal(a, b) for a, b in zip(parts, U.split(final)))
+    if not same:
+        raise RuntimeError("per-graph results differ from the batched form")
+    u1, s1 = aggregate(float(updates), t_union)
+    u2, s2 = aggregate(float(updates), t_each)
+    if rank != 0:
+        return
+    line = {"metric": "updates/s (256 independent graphs, batched form)", "value": round(u1 / s1, 1),
+            "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W, "ms_per_step": round(s1 / K * 1e3, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": "256 graphs, n log-uniform [1K, 256K], half ER half R-MAT, degree U[4,16], "
+                                   "seed 4; per step per graph: insert + delete batches of 1-10% of m (60/40)",
+                       "vertices": U.n, "edges": int(len(U.keys)), "updates_per_step": updates // K,
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "per_graph_launch_sequences": {"value": round(u2 / s2, 1), "ms_per_step": round(s2 / K * 1e3, 4),
+                                           "handles": len(graphs)},
+            "batched_over_per_graph": round((u1 / s1) / (u2 / s2), 2),
+            "results_identical": bool(same)}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(g, steps):
     """The serial oracle on the host cores, one step of the same trajectory
     (the first insert + delete batch from the initial state)."""
@@ -462,6 +555,8 @@ def main():
     rank, ws, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, rank, ws)
+    elif args.workload == "batched256":
+        run_batched(args, rank, ws, local)
     else:
         run_ours(args, rank, ws, local)
     import torch.distributed as dist

@@ -231,3 +231,72 @@ class Trajectory:
     def advance(self, batch: np.ndarray, op: int, parent: np.ndarray) -> None:
         self.keys = apply_keys(self.keys, batch, op)
         self.parent = np.ascontiguousarray(parent, np.int32).copy()
+
+
+# ------------------------------------------------------- many small graphs
+
+def batched_graphs(count: int = 256, seed: int = 4, n_lo: int = 1_000, n_hi: int = 256_000):
+    """Independent graphs with n log-uniform in [n_lo, n_hi] and average
+    degree uniform in [4, 16]; even indices Erdos-Renyi, odd R-MAT (sampled
+    at scale ceil(log2 n), endpoints >= n dropped after the permutation)."""
+    import math
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        deg = float(rng.uniform(4.0, 16.0))
+        gseed = (seed << 16) + i
+        if i % 2 == 0:
+            m = int(n * deg / 2)
+            keys = er(n, min(m, n * (n - 1) // 2), gseed)
+            out.append(Graph(f"er-{n}", n, keys))
+        else:
+            scale = max(1, math.ceil(math.log2(n)))
+            N = 1 << scale
+            ef = max(1, int(round(deg * N / (2.0 * n))))
+            keys = rmat(scale, ef, gseed, n=n)
+            out.append(Graph(f"rmat-{n}", n, keys))
+    return out
+
+
+class Union:
+    """Disjoint union of graphs with vertex-id offsets: one instance whose
+    update is the per-graph updates side by side."""
+
+    def __init__(self, graphs):
+        self.graphs = graphs
+        self.offsets = np.zeros(len(graphs) + 1, np.int64)
+        for i, g in enumerate(graphs):
+            self.offsets[i + 1] = self.offsets[i] + g.n
+        self.n = int(self.offsets[-1])
+        if self.n >= 2 ** 31:
+            raise ValueError("union too large for int32 ids")
+        ks, ps = [], []
+        for g, off in zip(graphs, self.offsets[:-1]):
+            o = np.uint64(off)
+            lo = (g.keys >> np.uint64(32)) + o
+            hi = (g.keys & np.uint64(0xFFFFFFFF)) + o
+            ks.append((lo << np.uint64(32)) | hi)
+            ps.append(g.parent.astype(np.int64) + off)
+        self.keys = np.sort(np.concatenate(ks)) if ks else np.zeros(0, np.uint64)
+        self.parent = np.concatenate(ps).astype(np.int32)
+
+    def shift(self, i: int, batch: np.ndarray) -> np.ndarray:
+        return (np.asarray(batch, np.int64) + self.offsets[i]).astype(np.int32)
+
+    def split(self, arr: np.ndarray):
+        """Per-graph slices of a union vertex array, ids shifted back."""
+        return [(arr[self.offsets[i]:self.offsets[i + 1]].astype(np.int64) - self.offsets[i]).astype(np.int32)
+                for i in range(len(self.graphs))]
+
+
+def batched_budgets(graphs, seed: int = 4, lo: float = 0.01, hi: float = 0.10, ins_frac: float = 0.6):
+    """Per graph one update budget of lo..hi of its m edges, split into an
+    insert batch size (ins_frac) and a delete batch size (the rest)."""
+    rng = np.random.default_rng(seed + 1)
+    out = []
+    for g in graphs:
+        budget = max(2, int(round(rng.uniform(lo, hi) * max(g.m, 1))))
+        b_ins = max(1, int(round(ins_frac * budget)))
+        out.append((b_ins, max(1, budget - b_ins)))
+    return out
