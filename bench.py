@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--batch", type=int, default=0, help="batch size (default per workload)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--euler", action="store_true", help="Euler-tour path marks (Algorithm 3)")
     return p.parse_args()
 
 
@@ -79,6 +80,7 @@ def workload_config(name, g, b):
     return {"workload": desc, "vertices": int(g.n), "edges": int(g.m), "batch": int(b),
             "step": f"one {b}-edge insert batch + one {b}-edge delete batch",
             "initial_forest": "FIFO BFS from each component's smallest id",
+            "reversal": "euler-tour intervals" if getattr(ARGS, "euler", False) else "pointer-doubling marks",
             "l2": "flushed between timed steps (256 MB write)"}
 
 
@@ -254,7 +256,8 @@ def run_ours(args, rank, ws, local):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
-    f = drsf.DynamicForest(g.n, edges_d, parent_d)
+    flags = drsf.DETERMINISTIC | (drsf.EULER_REVERSAL if args.euler else 0)
+    f = drsf.DynamicForest(g.n, edges_d, parent_d, flags=flags)
     for s in range(W):
         for op in (0, 1):
             f.apply(op, dev_batches[s][op])
@@ -550,8 +553,13 @@ def run_reference(args, rank, ws):
     print(json.dumps(line), flush=True)
 
 
+ARGS = None
+
+
 def main():
+    global ARGS
     args = parse()
+    ARGS = args
     rank, ws, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, rank, ws)

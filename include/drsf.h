@@ -82,7 +82,10 @@ enum {
     DRSF_DETERMINISTIC = 1u,
     /* drsf_create checks on the device that parent is a rooted spanning
      * forest of G and fails with DRSF_ENOT_FOREST otherwise (synchronises). */
-    DRSF_VALIDATE = 2u
+    DRSF_VALIDATE = 2u,
+    /* Mark the reversed paths with the Euler-tour intervals of the re-rooted
+     * trees (Algorithm 3) instead of pointer-doubling marks; same result. */
+    DRSF_EULER_REVERSAL = 4u
 };
 
 /* Per-batch counters of the last applied batch (drsf_stats). */

@@ -27,7 +27,7 @@ import torch
 from . import build as _build_mod
 
 INSERT, DELETE = 0, 1
-DETERMINISTIC, VALIDATE = 1, 2
+DETERMINISTIC, VALIDATE, EULER_REVERSAL = 1, 2, 4
 
 OK, EINVAL, ENOMEM, ECUDA, ENOT_FOREST, ETIMEOUT, EPOISONED = range(7)
 

@@ -54,7 +54,7 @@ struct drsf_ctx {
     int *chx = nullptr, *chy = nullptr;
     unsigned *aff_ep = nullptr, *cut_ep = nullptr, *pstamp = nullptr, *att_ep = nullptr, *rep_ep = nullptr;
     u64 *best0 = nullptr, *best1 = nullptr, *er = nullptr, *heavy = nullptr;
-    int *rold = nullptr, *cdeg = nullptr, *xlist = nullptr;
+    int *rold = nullptr, *cdeg = nullptr, *xlist = nullptr, *aidx = nullptr, *aroot = nullptr;
     long long *roff = nullptr;
     unsigned char *lf = nullptr;
     unsigned *wgt = nullptr;
@@ -423,6 +423,8 @@ static drsf_status alloc_work(drsf_ctx *h, cudaStream_t s) {
     CKA(halloc(h, &h->rold, n, s));
     CKA(halloc(h, &h->roff, n + 1, s));
     CKA(halloc(h, &h->xlist, n, s));
+    CKA(halloc(h, &h->aidx, n, s));
+    CKA(halloc(h, &h->aroot, n, s));
     CKA(halloc(h, &h->cdeg, n + 1, s));
     CKA(halloc(h, &h->lf, n + 1, s));
     CKA(halloc(h, &h->wgt, n, s));
@@ -557,6 +559,7 @@ drsf_status drsf_create(int32_t n, const int32_t *edges, int64_t m, const int32_
     h->dev.coop_orient = coop_blocks_orient(nsm);
     h->dev.coop_mark = coop_blocks_mark(nsm);
     h->dev.coop_bfs = coop_blocks_bfs(nsm);
+    h->dev.coop_et = coop_blocks_et(nsm);
     // DRSF_JUMP=halving selects the in-place path-halving root search
     const char *jm = getenv("DRSF_JUMP");
     h->jump_sync = (jm && strcmp(jm, "halving") == 0) ? 0 : 1;
@@ -651,13 +654,35 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
     prof_begin(h, PH_ACTIVE, s);
     if (op == DRSF_INSERT)
         CK(launch_active(h->dev, nullptr, 0, h->n, ctl, h->rep, h->parent, h->att_ep, h->att_x, h->rep_ep,
-                         h->newrep, h->act, h->pold, h->J0, h->mark, s));
+                         h->newrep, h->act, h->pold, h->J0, h->mark, h->aidx, h->aroot, s));
     else
         CK(launch_active(h->dev, h->A, 1, 0, ctl, h->rep, h->parent, h->att_ep, h->att_x, h->rep_ep, h->newrep,
-                         h->act, h->pold, h->J0, h->mark, s));
+                         h->act, h->pold, h->J0, h->mark, h->aidx, h->aroot, s));
     prof_end(h, PH_ACTIVE, 1, s);
     prof_begin(h, PH_MARK, s);
-    CK(launch_mark(h->dev, ctl, h->act, h->J0, h->J1, h->mark, h->parent, s));
+    if (h->flags & DRSF_EULER_REVERSAL) {
+        // Algorithm 3: Euler-tour intervals of the re-rooted pieces
+        EtArgs ea{};
+        ea.act = h->act;
+        ea.pold = h->pold;
+        ea.aidx = h->aidx;
+        ea.aroot = h->aroot;
+        ea.att_x = h->att_x;
+        ea.ccnt = h->pdeg;
+        ea.ccur = h->pcur;
+        ea.coff = h->poff;
+        ea.kids = h->adj;
+        ea.kpos = h->apos;
+        ea.val0 = h->val0;
+        ea.val1 = h->val1;
+        ea.nx0 = h->nx0;
+        ea.nx1 = h->nx1;
+        ea.bsum = h->bsum;
+        ea.mark = h->mark;
+        CK(launch_et_marks(h->dev, ctl, ea, s));
+    } else {
+        CK(launch_mark(h->dev, ctl, h->act, h->J0, h->J1, h->mark, h->parent, s));
+    }
     prof_end(h, PH_MARK, 1, s);
     prof_begin(h, PH_REVERSE, s);
     CK(launch_reverse(h->dev, ctl, h->act, h->pold, h->mark, h->chx, h->chy, h->parent, s));

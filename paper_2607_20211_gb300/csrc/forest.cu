@@ -651,7 +651,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
 // takes the super-tree's root as its new rep.
 __global__ void k_active(const int *L, int use_list, long long cnt_static, Ctl *ctl, int *rep, const int *parent,
                          const unsigned *att_ep, const int *att_x, const unsigned *rep_ep, const int *newrep,
-                         int *act, int *pold, int *J0, unsigned char *mark) {
+                         int *act, int *pold, int *J0, unsigned char *mark, int *aidx, int *aroot) {
     if (*(volatile int *)&ctl->skip) return;
     unsigned ep = ctl->epoch;
     long long cnt = use_list ? (long long)ctl->naff : cnt_static;
@@ -674,6 +674,8 @@ __global__ void k_active(const int *L, int use_list, long long cnt_static, Ctl *
             pold[q] = pv;
             J0[v] = pv;
             mark[v] = v == x;
+            aidx[v] = (int)q;   // dense index (Euler-tour marks)
+            aroot[q] = p;       // the piece root
         }
         if (i < cnt && rep_ep[p] == ep) rep[v] = newrep[p];
     }
@@ -818,10 +820,11 @@ cudaError_t launch_orient(const Dev &d, Ctl *ctl, OrientArgs a, cudaStream_t s) 
 }
 cudaError_t launch_active(const Dev &d, const int *L, int use_list, long long cnt_static, Ctl *ctl, int *rep,
                           const int *parent, const unsigned *att_ep, const int *att_x, const unsigned *rep_ep,
-                          const int *newrep, int *act, int *pold, int *J0, unsigned char *mark, cudaStream_t s) {
+                          const int *newrep, int *act, int *pold, int *J0, unsigned char *mark, int *aidx,
+                          int *aroot, cudaStream_t s) {
     unsigned g = use_list ? d.grid : gsz(cnt_static);
     k_active<<<g, BLK, 0, s>>>(L, use_list, cnt_static, ctl, rep, parent, att_ep, att_x, rep_ep, newrep, act,
-                                pold, J0, mark);
+                                pold, J0, mark, aidx, aroot);
     return cudaGetLastError();
 }
 cudaError_t launch_mark(const Dev &d, Ctl *ctl, const int *act, int *J0, int *J1, unsigned char *mark,

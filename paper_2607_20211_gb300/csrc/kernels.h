@@ -15,6 +15,7 @@ struct Dev {
     unsigned coop_orient;
     unsigned coop_mark;
     unsigned coop_bfs;
+    unsigned coop_et;
 };
 
 // graph.cu -------------------------------------------------------------
@@ -78,7 +79,8 @@ struct OrientArgs {
 cudaError_t launch_orient(const Dev &d, Ctl *ctl, OrientArgs a, cudaStream_t s);
 cudaError_t launch_active(const Dev &d, const int *L, int use_list, long long cnt_static, Ctl *ctl, int *rep,
                           const int *parent, const unsigned *att_ep, const int *att_x, const unsigned *rep_ep,
-                          const int *newrep, int *act, int *pold, int *J0, unsigned char *mark, cudaStream_t s);
+                          const int *newrep, int *act, int *pold, int *J0, unsigned char *mark, int *aidx,
+                          int *aroot, cudaStream_t s);
 cudaError_t launch_mark(const Dev &d, Ctl *ctl, const int *act, int *J0, int *J1, unsigned char *mark,
                         const int *parent, cudaStream_t s);
 cudaError_t launch_reverse(const Dev &d, Ctl *ctl, const int *act, const int *pold, const unsigned char *mark,
@@ -94,3 +96,13 @@ cudaError_t launch_barrier_selftest(Ctl *ctl, cudaStream_t s);
 cudaError_t launch_static_forest(const Dev &d, int n, Csr g, const u64 *ovf, Ctl *ctl, int *lab, int *comp,
                                  int *parent, int *f0, int *f1, u64 *levels, cudaStream_t s);
 unsigned coop_blocks_bfs(int nsm);
+// euler.cu -------------------------------------------------------------
+struct EtArgs {
+    const int *act, *pold, *aidx, *aroot, *att_x;
+    int *ccnt, *ccur, *coff, *kids, *kpos;
+    int *val0, *val1, *nx0, *nx1;
+    long long *bsum;
+    unsigned char *mark;
+};
+cudaError_t launch_et_marks(const Dev &d, Ctl *ctl, EtArgs a, cudaStream_t s);
+unsigned coop_blocks_et(int nsm);

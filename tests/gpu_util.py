@@ -41,9 +41,9 @@ def check_batch(f, n, keys, par, op, batch, labels=True):
     return ref.keys, ref.parent, st
 
 
-def run_trajectory(g, schedule, seed, tree_frac=0.5, local=0, labels=True):
+def run_trajectory(g, schedule, seed, tree_frac=0.5, local=0, labels=True, flags=drsf.DETERMINISTIC):
     """schedule: list of (op, batch size).  Returns the last GPU stats."""
-    f = make_forest(g)
+    f = make_forest(g, flags=flags)
     keys, par = g.keys, g.parent
     tr = workloads.Trajectory(g, seed, tree_frac=tree_frac, local=local)
     st = None
@@ -55,3 +55,12 @@ def run_trajectory(g, schedule, seed, tree_frac=0.5, local=0, labels=True):
     finally:
         f.close()
     return st
+
+
+def _tiny_graph(n, edges, parent):
+    """A Graph from an explicit edge list and parent array (None: BFS forest)."""
+    keys = workloads.edges_to_keys(np.array(edges, np.int64).reshape(-1, 2)) if edges else np.zeros(0, np.uint64)
+    g = workloads.Graph.__new__(workloads.Graph)
+    g.name, g.n, g.keys, g.W = "tiny", n, keys, 0
+    g.parent = np.array(parent, np.int32) if parent is not None else workloads.bfs_forest(n, keys)
+    return g
