@@ -191,7 +191,7 @@ static drsf_status build_graph(drsf_ctx *h, const int *edges, long long m, cudaS
                                long long *self_loops_out) {
     const int n = h->n;
     // index sized for load <= 0.5 with headroom for insertions
-    long long headroom = std::max<long long>(m / 2, 1 << 16);
+    long long headroom = std::max<long long>(m / 2, 1 << 12);
     u64 H = pow2_at_least((u64)(2 * (m + headroom)));
     Index ix{};
     CKA(halloc(h, &ix.key, H, s));
@@ -233,7 +233,7 @@ static drsf_status build_graph(drsf_ctx *h, const int *edges, long long m, cudaS
     CK(cudaMemsetAsync(used, 0, (size_t)n * sizeof(int), s));
     Csr g{off, used, col};
     CK(launch_fill(dkey, dslot, m2, g, ix, s));
-    u64 ovf_cap = std::max<u64>(1u << 20, (u64)m2 / 16);
+    u64 ovf_cap = std::max<u64>(1u << 16, (u64)m2 / 16);
     u64 *ovf = nullptr;
     CKA(halloc(h, &ovf, ovf_cap, s));
     // candidate buffers: every live undirected edge at most once
@@ -284,7 +284,7 @@ static drsf_status build_graph(drsf_ctx *h, const int *edges, long long m, cudaS
 
 static drsf_status ensure_batch(drsf_ctx *h, long long len, cudaStream_t s) {
     if (len <= h->batch_cap) return DRSF_OK;
-    long long cap = std::max<long long>(len, 1 << 16);
+    long long cap = std::max<long long>(len, 1 << 12);
     CK(cudaStreamSynchronize(s));
     hfree(h, &h->nkey, s);
     hfree(h, &h->nslot, s);
