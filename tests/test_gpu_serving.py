@@ -58,7 +58,7 @@ def _replay_alone(g, log):
     return out, par
 
 
-@pytest.mark.parametrize("coalesce,budget", [(True, 120 << 30), (False, 120 << 30), (True, 100 << 20)])
+@pytest.mark.parametrize("coalesce,budget", [(True, 120 << 30), (False, 120 << 30), (True, 20 << 20)])
 def test_mix_equals_alone(coalesce, budget):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
