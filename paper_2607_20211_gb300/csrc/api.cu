@@ -188,10 +188,11 @@ static u64 pow2_at_least(u64 x) {
 // Build the slack CSR, the edge index and the overflow list from an edge
 // list on the device (create and rebuild).  Synchronises `s`.
 static drsf_status build_graph(drsf_ctx *h, const int *edges, long long m, cudaStream_t s, long long *m_out,
-                               long long *self_loops_out) {
+                               long long *self_loops_out, long long extra) {
     const int n = h->n;
-    // index sized for load <= 0.5 with headroom for insertions
-    long long headroom = std::max<long long>(m / 2, 1 << 12);
+    // index sized for load <= 0.5 with headroom for insertions, at least
+    // twice the batch that asked for the rebuild
+    long long headroom = std::max<long long>(std::max<long long>(m / 2, 1 << 12), 2 * extra);
     u64 H = pow2_at_least((u64)(2 * (m + headroom)));
     Index ix{};
     CKA(halloc(h, &ix.key, H, s));
@@ -233,7 +234,7 @@ static drsf_status build_graph(drsf_ctx *h, const int *edges, long long m, cudaS
     CK(cudaMemsetAsync(used, 0, (size_t)n * sizeof(int), s));
     Csr g{off, used, col};
     CK(launch_fill(dkey, dslot, m2, g, ix, s));
-    u64 ovf_cap = std::max<u64>(1u << 16, (u64)m2 / 16);
+    u64 ovf_cap = std::max<u64>(std::max<u64>(1u << 16, (u64)m2 / 16), (u64)(2 * extra));
     u64 *ovf = nullptr;
     CKA(halloc(h, &ovf, ovf_cap, s));
     // candidate buffers: every live undirected edge at most once
@@ -313,7 +314,7 @@ static drsf_status read_ctl(drsf_ctx *h, cudaStream_t s) {
 
 // Extract the live edge list and rebuild CSR + index + overflow (compacts
 // deleted entries, absorbs overflow edges, resizes the index).
-static drsf_status rebuild(drsf_ctx *h, cudaStream_t s) {
+static drsf_status rebuild(drsf_ctx *h, cudaStream_t s, long long extra) {
     drsf_status st = read_ctl(h, s);
     if (st) return st;
     long long live = h->ctl_host->edges;
@@ -332,7 +333,7 @@ static drsf_status rebuild(drsf_ctx *h, cudaStream_t s) {
         return DRSF_EPOISONED;
     }
     long long m2 = 0;
-    st = build_graph(h, tmp, live, s, &m2, nullptr);
+    st = build_graph(h, tmp, live, s, &m2, nullptr, extra);
     hfree(h, &tmp, s);
     hfree(h, &cnt, s);
     if (st) return st;
@@ -363,7 +364,7 @@ static drsf_status storage_check(drsf_ctx *h, int op, long long len, cudaStream_
             h->occ_bound = occ;
             h->ovf_bound = ovfc;
             if (occ + len > (long long)(0.7 * (double)h->H) || ovfc + len > (long long)h->ovf_cap) {
-                st = rebuild(h, s);
+                st = rebuild(h, s, len);
                 if (st) return st;
             }
         }
@@ -379,7 +380,7 @@ static drsf_status storage_check(drsf_ctx *h, int op, long long len, cudaStream_
             long long ct = 2 * h->ctl_host->htomb + h->ctl_host->ctomb;
             h->ctomb_bound = ct;
             if (ct > h->col_cap / 4) {
-                st = rebuild(h, s);
+                st = rebuild(h, s, len);
                 if (st) return st;
             }
         }
@@ -488,7 +489,7 @@ static drsf_status create_impl(drsf_ctx *h, const int32_t *edges, int64_t m, con
     CK(cudaStreamSynchronize(s));
     if (hb[0] || hb[1]) return DRSF_EINVAL;
     long long m2 = 0, loops = 0;
-    st = build_graph(h, edges, m, s, &m2, &loops);
+    st = build_graph(h, edges, m, s, &m2, &loops, 0);
     if (st) return st;
     CK(cudaMemcpyAsync(h->parent, parent, (size_t)n * sizeof(int), cudaMemcpyDeviceToDevice, s));
     // representatives of F by pointer jumping over all vertices
