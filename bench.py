@@ -49,7 +49,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="rmat22",
-                   choices=["rmat22", "rmat20", "grid4096", "er-small", "batched256"])
+                   choices=["rmat22", "rmat20", "grid4096", "er-small", "batched256", "serving"])
+    p.add_argument("--requests", type=int, default=200, help="serving: requests in the trace")
+    p.add_argument("--load", type=float, default=0.9, help="serving: arrival rate / synchronous capacity")
     p.add_argument("--batch", type=int, default=0, help="batch size (default per workload)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -494,6 +496,90 @@ def run_batched(args, rank, ws, local):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, rank, ws, local):
+    """Serving: a resident R-MAT scale-22 graph plus 64 tenant R-MAT graphs
+    (scales 14-18, uniform), all kept on the device under a 120 GB budget; a
+    Poisson stream of update batches (sizes log-uniform in [100, 1M], 60%
+    insert / 40% delete, tenant Zipf(1.1) with rank 1 the resident graph,
+    seed 5).  The continuous-batching server is compared with synchronous
+    one-batch-at-a-time apply on the same trace and arrival times."""
+    import math
+    import torch
+    import paper_2607_20211_gb300 as drsf
+    import workloads
+    from paper_2607_20211_gb300 import serve
+    torch.cuda.set_device(local)
+    drsf.build()
+    rng = np.random.default_rng(5)
+    graphs = {0: workloads.rmat_graph(22, 16, seed=5)}
+    for i in range(1, 65):
+        graphs[i] = workloads.rmat_graph(int(rng.integers(14, 19)), 16, seed=5000 + i)
+    order = [0] + list(rng.permutation(np.arange(1, 65)))
+    zipf = np.array([1.0 / (k + 1) ** 1.1 for k in range(65)])
+    zipf /= zipf.sum()
+    # the trace: batches drawn along each tenant's own trajectory (planning on the GPU)
+    hs = {t: drsf.DynamicForest(g.n, torch.from_numpy(g.edges()).cuda(), torch.from_numpy(g.parent).cuda())
+          for t, g in graphs.items()}
+    trs = {t: workloads.Trajectory(g, seed=(5 << 20) + t) for t, g in graphs.items()}
+    reqs = []
+    for rid in range(args.requests):
+        t = int(order[rng.choice(65, p=zipf)])
+        op = int(rng.random() < 0.4)
+        size = int(round(math.exp(rng.uniform(math.log(100), math.log(1_000_000)))))
+        tr = trs[t]
+        if op == 1:
+            tr.parent = hs[t].parent().cpu().numpy()
+        batch = tr.next_batch(op, size)
+        hs[t].apply(op, torch.from_numpy(batch).cuda())
+        tr.keys = workloads.apply_keys(tr.keys, batch, op)
+        reqs.append(serve.Request(rid, t, op, batch, 0.0))
+    for h in hs.values():
+        h.close()
+    tenants = {t: (g.n, g.edges(), g.parent) for t, g in graphs.items()}
+    # capacity of the synchronous path (everything queued at time 0)
+    done0, hs0 = serve.run_synchronous(tenants, reqs)
+    for h in hs0.values():
+        h.close()
+    cap = len(reqs) / (max(d.t_done for d in done0))
+    lam = args.load * cap
+    arr = np.cumsum(rng.exponential(1.0 / lam, len(reqs)))
+    timed = [serve.Request(r.rid, r.tenant, r.op, r.batch, float(a)) for r, a in zip(reqs, arr)]
+    done_s, hs1 = serve.run_synchronous(tenants, timed)
+    sync_final = {t: h.parent().cpu().numpy() for t, h in hs1.items()}
+    for h in hs1.values():
+        h.close()
+    srv = serve.Server(budget_bytes=120 << 30, slots=8, coalesce=True)
+    for t, (n, e, p) in tenants.items():
+        srv.add_tenant(t, n, e, p)
+    done_c = srv.run(timed)
+    # each tenant's result in the mix equals its applied log replayed alone
+    same = True
+    for t, g in graphs.items():
+        _, par_mix = srv.state(t)
+        f = drsf.DynamicForest(g.n, torch.from_numpy(g.edges()).cuda(), torch.from_numpy(g.parent).cuda())
+        for op, b in srv.tenants[t].log:
+            f.apply_host(op, b)
+        same &= bool(np.array_equal(f.parent().cpu().numpy(), par_mix))
+        f.close()
+    sv, sy = serve.summarize(done_c), serve.summarize(done_s)
+    if rank != 0:
+        return
+    line = {"metric": "serving: sustained updates/s and batch latency (resident R-MAT-22 + 64 tenants)",
+            "value": sv["updates_per_s"], "unit": UNIT, "n_gpus": ws, "steps": len(reqs), "warmup": 0,
+            "ms_per_step": round(sv["makespan_s"] / len(reqs) * 1e3, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "resident R-MAT scale 22 + 64 R-MAT tenants (scales 14-18), 120 GB budget; "
+                                   "Poisson arrivals, sizes log-uniform [100, 1M], 60/40 insert/delete, "
+                                   "tenant Zipf(1.1), seed 5", "requests": len(reqs),
+                       "arrival_rate_per_s": round(lam, 2), "load_vs_sync_capacity": args.load,
+                       "slots": 8, "coalescing": True},
+            "server": sv, "synchronous": sy,
+            "server_over_sync_updates_per_s": round(sv["updates_per_s"] / sy["updates_per_s"], 3),
+            "coalesced_batches": int(sum(len(t.log) for t in srv.tenants.values())),
+            "evictions": srv.evictions, "results_identical_to_alone": same}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(g, steps):
     """The serial oracle on the host cores, one step of the same trajectory
     (the first insert + delete batch from the initial state)."""
@@ -565,6 +651,8 @@ def main():
         run_reference(args, rank, ws)
     elif args.workload == "batched256":
         run_batched(args, rank, ws, local)
+    elif args.workload == "serving":
+        run_serving(args, rank, ws, local)
     else:
         run_ours(args, rank, ws, local)
     import torch.distributed as dist
