@@ -551,6 +551,7 @@ def run_serving(args, rank, ws, local):
     srv = serve.Server(budget_bytes=120 << 30, slots=8, coalesce=True)
     for t, (n, e, p) in tenants.items():
         srv.add_tenant(t, n, e, p)
+    srv.admit_all()
     done_c = srv.run(timed)
     # each tenant's result in the mix equals its applied log replayed alone
     same = True

@@ -120,6 +120,17 @@ class Server:
         t.bytes = 0
         self.evictions += 1
 
+    def admit_all(self) -> int:
+        """Make tenants resident up front, in registration order, while the
+        budget allows (the resident set a serving run starts from).  Returns
+        the number admitted."""
+        k = 0
+        for t in self.tenants.values():
+            if t.handle is None and self.used + self._estimate(t) <= self.budget and self._admit(t):
+                k += 1
+        torch.cuda.synchronize()
+        return k
+
     def state(self, tid: int):
         """(edges, parent) of a tenant on the host."""
         t = self.tenants[tid]
