@@ -562,6 +562,17 @@ def run_serving(args, rank, ws, local):
             f.apply_host(op, b)
         same &= bool(np.array_equal(f.parent().cpu().numpy(), par_mix))
         f.close()
+    # saturation: everything queued at time 0 (capacity of each form)
+    srv2 = serve.Server(budget_bytes=120 << 30, slots=8, coalesce=True)
+    for t, (n, e, p) in tenants.items():
+        srv2.add_tenant(t, n, e, p)
+    srv2.admit_all()
+    done_c0 = srv2.run(reqs)
+    for t in srv2.tenants.values():
+        if t.handle is not None:
+            t.handle.close()
+    cap_server = serve.summarize(done_c0)
+    cap_sync = serve.summarize(done0)
     sv, sy = serve.summarize(done_c), serve.summarize(done_s)
     if rank != 0:
         return
@@ -575,6 +586,10 @@ def run_serving(args, rank, ws, local):
                        "arrival_rate_per_s": round(lam, 2), "load_vs_sync_capacity": args.load,
                        "slots": 8, "coalescing": True},
             "server": sv, "synchronous": sy,
+            "capacity": {"server_updates_per_s": cap_server["updates_per_s"],
+                         "synchronous_updates_per_s": cap_sync["updates_per_s"],
+                         "server_over_sync": round(cap_server["updates_per_s"] / cap_sync["updates_per_s"], 3),
+                         "what": "all requests queued at time 0"},
             "server_over_sync_updates_per_s": round(sv["updates_per_s"] / sy["updates_per_s"], 3),
             "coalesced_batches": int(sum(len(t.log) for t in srv.tenants.values())),
             "evictions": srv.evictions, "results_identical_to_alone": same}
