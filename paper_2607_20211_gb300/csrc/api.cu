@@ -55,6 +55,7 @@ struct drsf_ctx {
     unsigned *aff_ep = nullptr, *cut_ep = nullptr, *pstamp = nullptr, *att_ep = nullptr, *rep_ep = nullptr;
     u64 *best0 = nullptr, *best1 = nullptr, *er = nullptr, *heavy = nullptr;
     int *rold = nullptr, *cdeg = nullptr, *xlist = nullptr, *aidx = nullptr, *aroot = nullptr;
+    int *oep = nullptr, *oeid = nullptr, *oeroot = nullptr;
     long long *roff = nullptr;
     unsigned char *lf = nullptr;
     unsigned *wgt = nullptr;
@@ -295,8 +296,9 @@ static drsf_status ensure_batch(drsf_ctx *h, long long len, cudaStream_t s) {
     CKA(halloc(h, &h->nkey, (size_t)cap, s));
     CKA(halloc(h, &h->nslot, (size_t)cap, s));
     CKA(halloc(h, &h->cutlist, (size_t)cap, s));
-    // pair table: room for ~8 piece pairs per batch edge at load <= 1/2
-    u64 T = pow2_at_least((u64)cap * 16);
+    // pair table: room for ~2 piece pairs per batch edge at load <= 1/2
+    // (a pair that finds no slot falls back to a plain candidate)
+    u64 T = pow2_at_least((u64)cap * 4);
     CKA(halloc(h, &h->pt.pk, T, s));
     CKA(halloc(h, &h->pt.mk, T, s));
     CK(cudaMemsetAsync(h->pt.pk, 0xFF, T * sizeof(u64), s));
@@ -426,6 +428,9 @@ static drsf_status alloc_work(drsf_ctx *h, cudaStream_t s) {
     CKA(halloc(h, &h->xlist, n, s));
     CKA(halloc(h, &h->aidx, n, s));
     CKA(halloc(h, &h->aroot, n, s));
+    CKA(halloc(h, &h->oep, 2 * n + 2, s));
+    CKA(halloc(h, &h->oeid, 2 * n + 2, s));
+    CKA(halloc(h, &h->oeroot, n + 1, s));
     CKA(halloc(h, &h->cdeg, n + 1, s));
     CKA(halloc(h, &h->lf, n + 1, s));
     CKA(halloc(h, &h->wgt, n, s));
@@ -496,7 +501,7 @@ static drsf_status create_impl(drsf_ctx *h, const int32_t *edges, int64_t m, con
     CK(launch_copy_parent(n, h->parent, h->J0, s));
     Csr g0{h->off, h->used, h->col};
     CK(launch_jump(h->dev, nullptr, 0, n, h->ctl, h->J0, h->J1, h->rep, h->D, 0, h->rold, h->wgt, h->heavy, g0,
-                   h->roff, h->bsum, h->jump_sync, h->act, h->xlist, s));
+                   h->roff, h->bsum, h->jump_sync, h->act, h->xlist, h->cutlist, s));
     Ctl c{};
     CK(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -610,7 +615,7 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
         prof_end(h, PH_AFF, 1, s);
         prof_begin(h, PH_JUMP, s);
         CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->J0, h->J1, h->rep, h->D, 1, h->rold, h->wgt, h->heavy, g,
-                       h->roff, h->bsum, h->jump_sync, h->act, h->xlist, s));
+                       h->roff, h->bsum, h->jump_sync, h->act, h->xlist, h->cutlist, s));
         prof_end(h, PH_JUMP, 1, s);
         prof_begin(h, PH_SCAN, s);
         CK(launch_scan_rows(h->dev, h->D, h->roff, ctl, g, h->rep, h->rold, h->heavy, h->pt, h->ck[0], h->ca[0],
@@ -649,6 +654,9 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
     oa.newrep = h->newrep;
     oa.lf = h->lf;
     oa.cdeg = h->cdeg;
+    oa.ep = h->oep;
+    oa.eid = h->oeid;
+    oa.eroot = h->oeroot;
     prof_begin(h, PH_ORIENT, s);
     CK(launch_orient(h->dev, ctl, oa, s));
     prof_end(h, PH_ORIENT, 1, s);

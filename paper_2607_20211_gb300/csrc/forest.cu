@@ -20,6 +20,7 @@
 // cores of up to this many arcs are list-ranked in one block's shared memory
 #define ORIENT_SMEM_ARCS 12288
 #define ORIENT_SMEM_BYTES (4 * ORIENT_SMEM_ARCS * (int)sizeof(int))
+#define ORIENT_THREADS 1024
 
 #define GS_LOOP(i, n) \
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)(n); \
@@ -99,7 +100,7 @@ __device__ __forceinline__ int find_halving(int *J, int v, Ctl *ctl) {
 // their lengths in roff (roff[ndet] = total) for the load-balanced scan.
 __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1, int *rep,
                        int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g, long long *roff,
-                       long long *bsum, int sync_rounds, int *X, int *Y) {
+                       long long *bsum, int sync_rounds, int *X, int *Y, const int *cuts) {
     if (*(volatile int *)&ctl->skip) return;
     long long cnt = use_list ? (long long)ctl->naff : cnt_static;
     if (sync_rounds) {
@@ -167,10 +168,11 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
             }
             return;
         }
-        // final pass: representatives and piece weights (sum of row lengths
-        // + 1 per vertex; weights of piece roots were zeroed at the cut);
-        // the dominant piece of the block is summed in shared memory (one
-        // global atomic per block for it)
+        // final pass: representatives, piece weights (sum of row lengths + 1
+        // per vertex; weights of piece roots were zeroed at the cut), and a
+        // provisional list of rows to scan: every vertex outside its tree's
+        // root piece.  The dominant piece of the block is summed in shared
+        // memory (one global atomic per block for it).
         __shared__ int s_p;
         __shared__ unsigned s_sum;
         if (threadIdx.x == 0) {
@@ -178,19 +180,34 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
             s_sum = 0;
         }
         __syncthreads();
-        for (long long i = gtid(); i < cnt; i += gstride()) {
-            int v = A[i];
-            int p = ~LD(Jc[v]);
-            rep[v] = p;
-            long long cap = g.off[v + 1] - g.off[v];
-            long long used = g.used[v];
-            unsigned d = (unsigned)(used < cap ? used : cap) + 1u;
-            unsigned grp = __match_any_sync(__activemask(), p);
-            unsigned tot = __reduce_add_sync(grp, d);
-            if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
-                if (*(volatile int *)&s_p == -1) atomicCAS(&s_p, -1, p);
-                if (*(volatile int *)&s_p == p) atomicAdd(&s_sum, tot);
-                else atomicAdd(&w[p], tot);
+        for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += gstride()) {
+            long long i = base + threadIdx.x;
+            bool valid = i < cnt, scan = false;
+            int v = 0, p = 0;
+            long long len = 0;
+            if (valid) {
+                v = A[i];
+                p = ~LD(Jc[v]);
+                rep[v] = p;
+                long long cap = g.off[v + 1] - g.off[v];
+                long long used = g.used[v];
+                len = used < cap ? used : cap;
+                scan = p != rold[v] && len > 0;
+            }
+            unsigned vm = __ballot_sync(0xffffffffu, valid);
+            if (valid) {
+                unsigned grp = __match_any_sync(vm, p);
+                unsigned tot = __reduce_add_sync(grp, (unsigned)len + 1u);
+                if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
+                    if (*(volatile int *)&s_p == -1) atomicCAS(&s_p, -1, p);
+                    if (*(volatile int *)&s_p == p) atomicAdd(&s_sum, tot);
+                    else atomicAdd(&w[p], tot);
+                }
+            }
+            long long q = block_append(&ctl->ndet, scan);
+            if (scan) {
+                D[q] = v;
+                roff[q] = len;
             }
         }
         __syncthreads();
@@ -217,28 +234,59 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
         }
     }
     if (!grid_barrier(ctl, &ctl->bar[0])) return;
-    for (long long i = gtid(); i < cnt; i += gstride()) {
-        int v = A[i];
-        if (LD(rep[v]) == v) atomicMax(&heavy[rold[v]], ((u64)LD(w[v]) << 32) | (unsigned)v);
+    // heaviest piece per cut tree: its pieces are the root piece and one
+    // piece per cut vertex, so the cut list covers them all
+    const long long nc = (long long)ctl->ncut;
+    for (long long i = gtid(); i < nc; i += gstride()) {
+        int c = cuts[i];
+        int r = rold[c];
+        u64 kc = ((u64)LD(w[c]) << 32) | (unsigned)c;
+        unsigned act = __activemask();
+        unsigned grp = __match_any_sync(act, r);
+        unsigned hi = (unsigned)(kc >> 32), lo = (unsigned)kc;
+        unsigned hmax = __reduce_max_sync(grp, hi);
+        unsigned lmax = __reduce_max_sync(grp, hi == hmax ? lo : 0u);
+        if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
+            atomicMax(&heavy[r], ((u64)hmax << 32) | lmax);
+            atomicMax(&heavy[r], ((u64)LD(w[r]) << 32) | (unsigned)r);
+        }
     }
     if (!grid_barrier(ctl, &ctl->bar[0])) return;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += gstride()) {
-        long long i = base + threadIdx.x;
-        bool scan = false;
-        int v = 0;
-        long long len = 0;
-        if (i < cnt) {
-            v = A[i];
-            int hp = (int)(unsigned)LD(heavy[rold[v]]);
-            long long cap = g.off[v + 1] - g.off[v];
-            long long used = g.used[v];
-            len = used < cap ? used : cap;
-            scan = LD(rep[v]) != hp && len > 0;
+    // the provisional list left out each tree's root piece; where another
+    // piece is heavier, rebuild the list with the exact rule (rare)
+    if (gtid() == 0) ctl->flag[0] = 0;
+    if (!grid_barrier(ctl, &ctl->bar[0])) return;
+    {
+        bool swap = false;
+        for (long long i = gtid(); i < nc; i += gstride()) {
+            int r = rold[cuts[i]];
+            swap |= (int)(unsigned)LD(heavy[r]) != r;
         }
-        long long p = block_append(&ctl->ndet, scan);
-        if (scan) {
-            D[p] = v;
-            roff[p] = len;
+        // (the halving root search builds no provisional list: always exact)
+        if (__syncthreads_or(swap || !sync_rounds) && threadIdx.x == 0) atomicOr(&ctl->flag[0], 1);
+    }
+    if (!grid_barrier(ctl, &ctl->bar[0])) return;
+    if (*(volatile int *)&ctl->flag[0]) {
+        if (gtid() == 0) ctl->ndet = 0;
+        if (!grid_barrier(ctl, &ctl->bar[0])) return;
+        for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += gstride()) {
+            long long i = base + threadIdx.x;
+            bool scan = false;
+            int v = 0;
+            long long len = 0;
+            if (i < cnt) {
+                v = A[i];
+                int hp = (int)(unsigned)LD(heavy[rold[v]]);
+                long long cap = g.off[v + 1] - g.off[v];
+                long long used = g.used[v];
+                len = used < cap ? used : cap;
+                scan = LD(rep[v]) != hp && len > 0;
+            }
+            long long q = block_append(&ctl->ndet, scan);
+            if (scan) {
+                D[q] = v;
+                roff[q] = len;
+            }
         }
     }
     if (!grid_barrier(ctl, &ctl->bar[0])) return;
@@ -417,14 +465,20 @@ __device__ int block_excl_scan(int v, int *total) {
 // each edge is oriented by its arc that comes first.  The child piece P of
 // edge {x, y} (x in P) gets the oriented replacement edge x -> y; every piece
 // of the super-tree gets the root as its new representative.
-__global__ void k_orient(Ctl *ctl, OrientArgs a) {
+__global__ void __launch_bounds__(ORIENT_THREADS) k_orient(Ctl *ctl, OrientArgs a) {
     if (*(volatile int *)&ctl->skip) return;
     const long long ner = (long long)ctl->ner;
     const unsigned ep = ctl->epoch;
-    // phase 1: dense ids for the pieces touched by E_r, minp init
-    for (long long i = gtid(); i < 2 * ner; i += gstride()) {
-        u64 k = a.er[i >> 1];
-        int p = a.rep[(i & 1) ? khi(k) : klo(k)];
+    u64 *bar = &ctl->bar[2];
+    // Arc j of edge j/2 runs from the piece of its (j odd ? larger : smaller)
+    // endpoint to the other piece.  Phase 1 caches each arc's source piece
+    // (ep), later phases its dense id (eid) and each edge's super-tree root
+    // (eroot), so no phase re-walks rep / pidx / the hook forest.
+    // phase 1: dense ids for the pieces touched by E_r
+    for (long long j = gtid(); j < 2 * ner; j += gstride()) {
+        u64 k = a.er[j >> 1];
+        int p = a.rep[(j & 1) ? khi(k) : klo(k)];
+        a.ep[j] = p;
         bool first = atomicExch(&a.pstamp[p], ep) != ep;
         long long id = agg_append(&ctl->npc, first);
         if (first) {
@@ -433,35 +487,35 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
             a.pdeg[id] = 0;
             a.cdeg[id] = 0;
             a.pcur[id] = 0;
-            // the root piece of the hook forest holds its super-tree's slot;
-            // one write per super-tree (many threads share one root)
+            // the root piece of the hook forest holds its super-tree's slot
             if (find_root(a.comp, p, ctl) == p) a.minp[p] = INT_MAX;
         }
     }
-    if (!grid_barrier(ctl, &ctl->bar[2])) return;
+    if (!grid_barrier(ctl, bar)) return;
     // phase 2: smallest piece id per super-tree, degrees (lanes with the
     // same target combine first: one super-tree or piece can collect most
     // of the batch's edges)
-    for (long long i = gtid(); i < 2 * ner; i += gstride()) {
-        u64 k = a.er[i >> 1];
-        int p = a.rep[(i & 1) ? khi(k) : klo(k)];
+    for (long long j = gtid(); j < 2 * ner; j += gstride()) {
+        int p = LD(a.ep[j]);
+        int id = LD(a.pidx[p]);
         int root = find_root(a.comp, p, ctl);
+        a.eid[j] = id;
+        if (!(j & 1)) a.eroot[j >> 1] = root;
         unsigned act = __activemask();
         unsigned g1 = __match_any_sync(act, root);
         int pm = (int)__reduce_min_sync(g1, (unsigned)p);
         if ((int)(threadIdx.x & 31) == __ffs(g1) - 1) atomicMin(&a.minp[root], pm);
-        int id = LD(a.pidx[p]);
         unsigned g2 = __match_any_sync(act, id);
         if ((int)(threadIdx.x & 31) == __ffs(g2) - 1) atomicAdd(&a.pdeg[id], __popc(g2));
     }
-    if (!grid_barrier(ctl, &ctl->bar[2])) return;
-    // phase 2b: leaf edges; core degrees
+    if (!grid_barrier(ctl, bar)) return;
+    // phase 2b: leaf edges (a non-root piece with one edge); core degrees
     for (long long i = gtid(); i < ner; i += gstride()) {
-        u64 k = a.er[i];
-        int p0 = a.rep[klo(k)], p1 = a.rep[khi(k)];
-        int id0 = LD(a.pidx[p0]), id1 = LD(a.pidx[p1]);
-        bool leaf0 = LD(a.pdeg[id0]) == 1 && LD(a.minp[find_root(a.comp, p0, ctl)]) != p0;
-        bool leaf1 = LD(a.pdeg[id1]) == 1 && LD(a.minp[find_root(a.comp, p1, ctl)]) != p1;
+        int p0 = LD(a.ep[2 * i]), p1 = LD(a.ep[2 * i + 1]);
+        int id0 = LD(a.eid[2 * i]), id1 = LD(a.eid[2 * i + 1]);
+        int sr = LD(a.minp[LD(a.eroot[i])]);
+        bool leaf0 = LD(a.pdeg[id0]) == 1 && sr != p0;
+        bool leaf1 = LD(a.pdeg[id1]) == 1 && sr != p1;
         unsigned char lf = leaf0 ? 1 : (leaf1 ? 2 : 0);
         a.lf[i] = lf;
         unsigned act = __activemask();
@@ -473,89 +527,85 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
             if ((int)(threadIdx.x & 31) == __ffs(g1) - 1) atomicAdd(&a.cdeg[id1], __popc(g1));
         }
     }
-    if (!grid_barrier(ctl, &ctl->bar[2])) return;
+    if (!grid_barrier(ctl, bar)) return;
     // phase 3: exclusive scan of core degrees -> adjacency offsets
     const long long np = (long long)*(volatile u64 *)&ctl->npc;
     const long long chunk = (np + gridDim.x - 1) / gridDim.x;
     const long long lo = (long long)blockIdx.x * chunk, hi = lo + chunk < np ? lo + chunk : np;
     {
-        int s = 0;
-        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) s += LD(a.cdeg[i]);
-        int tot;
-        block_excl_scan(s, &tot);
+        long long sacc = 0;
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) sacc += LD(a.cdeg[i]);
+        long long tot;
+        block_excl_scan_ll(sacc, &tot);
         if (threadIdx.x == 0) a.bsum[blockIdx.x] = tot;
     }
-    if (!grid_barrier(ctl, &ctl->bar[2])) return;
+    if (!grid_barrier(ctl, bar)) return;
     if (blockIdx.x == 0) {
         long long nbk = gridDim.x;
-        long long per = (nbk + BLK - 1) / BLK;
+        long long per = (nbk + blockDim.x - 1) / blockDim.x;
         long long l0 = threadIdx.x * per, l1 = l0 + per < nbk ? l0 + per : nbk;
-        int s = 0;
-        for (long long i = l0; i < l1; ++i) s += (int)LD(a.bsum[i]);
-        int tot;
-        int pre = block_excl_scan(s, &tot);
+        long long sacc = 0;
+        for (long long i = l0; i < l1; ++i) sacc += LD(a.bsum[i]);
+        long long tot;
+        long long pre = block_excl_scan_ll(sacc, &tot);
         for (long long i = l0; i < l1; ++i) {
             long long t = LD(a.bsum[i]);
             a.bsum[i] = pre;
-            pre += (int)t;
+            pre += t;
         }
         if (threadIdx.x == 0) ctl->ncore = (u64)tot;   // core arcs = slots of the core adjacency
     }
-    if (!grid_barrier(ctl, &ctl->bar[2])) return;
+    if (!grid_barrier(ctl, bar)) return;
     {
-        int carry = (int)LD(a.bsum[blockIdx.x]);
+        long long carry = LD(a.bsum[blockIdx.x]);
         for (long long t0 = lo; t0 < hi; t0 += blockDim.x) {
             long long i = t0 + threadIdx.x;
-            int d = i < hi ? LD(a.cdeg[i]) : 0;
-            int tot;
-            int pre = block_excl_scan(d, &tot);
-            if (i < hi) a.poff[i] = carry + pre;
+            long long d = i < hi ? LD(a.cdeg[i]) : 0;
+            long long tot;
+            long long pre = block_excl_scan_ll(d, &tot);
+            if (i < hi) a.poff[i] = (int)(carry + pre);
             carry += tot;
         }
     }
-    if (!grid_barrier(ctl, &ctl->bar[2])) return;
-    // phase 4: place core arcs; arc 2i = (lo-piece -> hi-piece), 2i+1 its twin
-    for (long long i = gtid(); i < 2 * ner; i += gstride()) {
-        bool core = !LD(a.lf[i >> 1]);
+    if (!grid_barrier(ctl, bar)) return;
+    // phase 4: place core arcs in their source piece's adjacency
+    for (long long j = gtid(); j < 2 * ner; j += gstride()) {
+        bool core = !LD(a.lf[j >> 1]);
         unsigned cm = __ballot_sync(__activemask(), core);
         if (!core) continue;
-        u64 k = a.er[i >> 1];
-        int p = a.rep[(i & 1) ? khi(k) : klo(k)];
-        int id = LD(a.pidx[p]);
+        int id = LD(a.eid[j]);
         unsigned grp = __match_any_sync(cm, id);
         int lane = threadIdx.x & 31, leader = __ffs(grp) - 1;
         int base = 0;
         if (lane == leader) base = atomicAdd(&a.pcur[id], __popc(grp));
         base = __shfl_sync(grp, base, leader);
         int slot = LD(a.poff[id]) + base + __popc(grp & ((1u << lane) - 1u));
-        a.adj[slot] = (int)i;
-        a.apos[i] = slot;
+        a.adj[slot] = (int)j;
+        a.apos[j] = slot;
     }
-    if (!grid_barrier(ctl, &ctl->bar[2])) return;
+    if (!grid_barrier(ctl, bar)) return;
     // phase 5: Euler successors of core arcs, in slot space (the position of
     // an arc in the core adjacency array): the successor of arc a->b is the
     // slot after b->a's slot in b's list, wrapping to the list start; the
     // circuit is opened at each super-tree root
-    for (long long i = gtid(); i < 2 * ner; i += gstride()) {
-        if (LD(a.lf[i >> 1])) continue;
-        long long tw = i ^ 1;
-        u64 k = a.er[i >> 1];
-        int head = a.rep[(i & 1) ? klo(k) : khi(k)];     // source of the twin
-        int id = LD(a.pidx[head]);
-        int start = LD(a.poff[id]), end = start + LD(a.cdeg[id]);
+    for (long long j = gtid(); j < 2 * ner; j += gstride()) {
+        if (LD(a.lf[j >> 1])) continue;
+        long long tw = j ^ 1;
+        int hid = LD(a.eid[tw]);                  // the arc's head = the twin's source
+        int start = LD(a.poff[hid]), end = start + LD(a.cdeg[hid]);
         int nx = LD(a.apos[tw]) + 1;
         int succ;
         if (nx == end) {
-            bool is_root = LD(a.minp[find_root(a.comp, head, ctl)]) == head;
+            bool is_root = LD(a.minp[LD(a.eroot[j >> 1])]) == LD(a.ep[tw]);
             succ = is_root ? NIL : start;
         } else {
             succ = nx;
         }
-        int si = LD(a.apos[i]);
+        int si = LD(a.apos[j]);
         a.nx0[si] = succ;
         a.val0[si] = 1;
     }
-    if (!grid_barrier(ctl, &ctl->bar[2])) return;
+    if (!grid_barrier(ctl, bar)) return;
     // phase 6: list ranking (Wyllie): val = arcs from here to the tour end.
     // A core of at most ORIENT_SMEM_ARCS arcs is ranked by block 0 alone in
     // shared memory (block barriers instead of grid barriers per round).
@@ -593,7 +643,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
             for (long long i = threadIdx.x; i < ncore; i += blockDim.x) a.val0[i] = svc[i];
             if (threadIdx.x == 0) ctl->rank_rounds = r + 1;
         }
-        if (!grid_barrier(ctl, &ctl->bar[2])) return;
+        if (!grid_barrier(ctl, bar)) return;
         vc = a.val0;
     } else {
         for (;; ++r) {
@@ -615,7 +665,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
                 }
             }
             if (__syncthreads_or(ch) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
-            if (!grid_barrier(ctl, &ctl->bar[2])) return;
+            if (!grid_barrier(ctl, bar)) return;
             int again = *(volatile int *)&ctl->flag[r % 3];
             int *t = vc; vc = vn; vn = t;
             t = nc; nc = nn; nn = t;
@@ -627,7 +677,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
     for (long long i = gtid(); i < ner; i += gstride()) {
         u64 k = a.er[i];
         int x0 = (int)klo(k), x1 = (int)khi(k);
-        int p0 = a.rep[x0], p1 = a.rep[x1];
+        int p0 = LD(a.ep[2 * i]), p1 = LD(a.ep[2 * i + 1]);
         unsigned char lf = LD(a.lf[i]);
         bool down;                                 // true: p0 is the parent of p1
         if (lf) down = lf == 2;
@@ -640,7 +690,7 @@ __global__ void k_orient(Ctl *ctl, OrientArgs a) {
         // per piece; the super-root keeps its representative
         a.att_x[child] = x;
         a.att_ep[child] = ep;
-        a.newrep[child] = LD(a.minp[find_root(a.comp, p0, ctl)]);
+        a.newrep[child] = LD(a.minp[LD(a.eroot[i])]);
         a.rep_ep[child] = ep;
     }
 }
@@ -778,8 +828,9 @@ unsigned coop_blocks_hook(int nsm) { return coop_blocks((const void *)k_boruvka,
 unsigned coop_blocks_orient(int nsm) {
     cudaFuncSetAttribute((const void *)k_orient, cudaFuncAttributeMaxDynamicSharedMemorySize, ORIENT_SMEM_BYTES);
     int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k_orient, BLK, ORIENT_SMEM_BYTES) !=
-            cudaSuccess || per < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k_orient, ORIENT_THREADS,
+                                                      ORIENT_SMEM_BYTES) != cudaSuccess ||
+        per < 1)
         per = 1;
     if (per > 2) per = 2;
     return (unsigned)(per * nsm);
@@ -802,10 +853,12 @@ cudaError_t launch_copy_parent(int n, const int *parent, int *J0, cudaStream_t s
 }
 cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1,
                         int *rep, int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g,
-                        long long *roff, long long *bsum, int sync_rounds, int *X, int *Y, cudaStream_t s) {
+                        long long *roff, long long *bsum, int sync_rounds, int *X, int *Y, const int *cuts,
+                        cudaStream_t s) {
     void *args[] = {(void *)&A, (void *)&use_list, (void *)&cnt_static, (void *)&ctl, (void *)&J, (void *)&J1,
                     (void *)&rep, (void *)&D, (void *)&mode, (void *)&rold, (void *)&w, (void *)&heavy,
-                    (void *)&g, (void *)&roff, (void *)&bsum, (void *)&sync_rounds, (void *)&X, (void *)&Y};
+                    (void *)&g, (void *)&roff, (void *)&bsum, (void *)&sync_rounds, (void *)&X, (void *)&Y,
+                    (void *)&cuts};
     return cudaLaunchCooperativeKernel((const void *)k_jump, d.coop_jump, BLK, args, 0, s);
 }
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
@@ -816,7 +869,8 @@ cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0,
 }
 cudaError_t launch_orient(const Dev &d, Ctl *ctl, OrientArgs a, cudaStream_t s) {
     void *args[] = {(void *)&ctl, (void *)&a};
-    return cudaLaunchCooperativeKernel((const void *)k_orient, d.coop_orient, BLK, args, ORIENT_SMEM_BYTES, s);
+    return cudaLaunchCooperativeKernel((const void *)k_orient, d.coop_orient, ORIENT_THREADS, args,
+                                       ORIENT_SMEM_BYTES, s);
 }
 cudaError_t launch_active(const Dev &d, const int *L, int use_list, long long cnt_static, Ctl *ctl, int *rep,
                           const int *parent, const unsigned *att_ep, const int *att_x, const unsigned *rep_ep,

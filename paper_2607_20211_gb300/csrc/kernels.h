@@ -59,7 +59,8 @@ cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsign
 cudaError_t launch_copy_parent(int n, const int *parent, int *J0, cudaStream_t s);
 cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1,
                         int *rep, int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g,
-                        long long *roff, long long *bsum, int sync_rounds, int *X, int *Y, cudaStream_t s);
+                        long long *roff, long long *bsum, int sync_rounds, int *X, int *Y, const int *cuts,
+                        cudaStream_t s);
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
                            int *comp, u64 *best0, u64 *best1, u64 *er, long long er_cap, cudaStream_t s);
 struct OrientArgs {
@@ -75,6 +76,8 @@ struct OrientArgs {
     int *att_x, *newrep;
     unsigned char *lf;   // per replacement edge: 0 core, 1 lo-side piece is a leaf, 2 hi-side
     int *cdeg;           // core degree per dense piece
+    int *ep, *eid;       // per arc: source piece, its dense id
+    int *eroot;          // per edge: hook-forest root of its super-tree
 };
 cudaError_t launch_orient(const Dev &d, Ctl *ctl, OrientArgs a, cudaStream_t s);
 cudaError_t launch_active(const Dev &d, const int *L, int use_list, long long cnt_static, Ctl *ctl, int *rep,
