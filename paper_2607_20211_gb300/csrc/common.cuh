@@ -211,6 +211,20 @@ __device__ __forceinline__ long long block_excl_scan_ll(long long v, long long *
     return pre;
 }
 
+// Block-aggregated reservation of `cnt` consecutive slots per thread (one
+// atomicAdd per block); returns this thread's first slot.  Every thread of
+// the block must call it.
+__device__ __forceinline__ long long block_reserve(u64 *ctr, int cnt) {
+    __shared__ u64 s_rb;
+    long long tot;
+    long long pre = block_excl_scan_ll(cnt, &tot);
+    if (threadIdx.x == 0) s_rb = tot ? atomicAdd(ctr, (u64)tot) : 0;
+    __syncthreads();
+    long long r = (long long)s_rb + pre;
+    __syncthreads();
+    return r;
+}
+
 // 64-bit minimum over a group of lanes (mask from __match_any_sync).
 __device__ __forceinline__ u64 group_min_u64(unsigned grp, u64 k) {
     unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;

@@ -21,6 +21,8 @@
 #define ORIENT_SMEM_ARCS 12288
 #define ORIENT_SMEM_BYTES (4 * ORIENT_SMEM_ARCS * (int)sizeof(int))
 #define ORIENT_THREADS 1024
+// independent items per thread and iteration in the pointer-doubling rounds
+#define JU 4
 
 #define GS_LOOP(i, n) \
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)(n); \
@@ -133,29 +135,43 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
             }
             const int *in = r == 0 ? (use_list ? A : nullptr) : ((r & 1) ? X : Y);
             int *out = (r & 1) ? Y : X;
-            for (long long base = (long long)blockIdx.x * blockDim.x; base < c; base += gstride()) {
-                long long i = base + threadIdx.x;
-                bool open = false;
-                int v = 0, nv = 0;
-                if (i < c) {
-                    v = in ? in[i] : (int)i;
-                    int w0 = LD(Jc[v]);
-                    if (w0 < 0) {
-                        nv = w0;
-                    } else {
-                        int w2 = LD(Jc[w0]);
-                        if (w2 < 0) nv = w2;
-                        else if (w2 == w0) nv = ~w0;
-                        else {
-                            nv = w2;
-                            open = true;
-                        }
-                    }
-                    Jn[v] = nv;
-                    if (!open) Jc[v] = nv;
+            // JU independent vertices per thread and iteration: their loads
+            // are issued together (more loads in flight per thread)
+            const long long S = gstride();
+            for (long long base = (long long)blockIdx.x * blockDim.x; base < c; base += S * JU) {
+                int v[JU], w0[JU], w2[JU];
+                bool ok[JU], open[JU];
+#pragma unroll
+                for (int k = 0; k < JU; ++k) {
+                    long long i = base + k * S + threadIdx.x;
+                    ok[k] = i < c;
+                    v[k] = ok[k] ? (in ? in[i] : (int)i) : 0;
                 }
-                long long q = block_append(&ctl->cnt[(r + 1) % 3], open);
-                if (open) out[q] = v;
+#pragma unroll
+                for (int k = 0; k < JU; ++k) w0[k] = ok[k] ? LD(Jc[v[k]]) : -1;
+#pragma unroll
+                for (int k = 0; k < JU; ++k) w2[k] = (ok[k] && w0[k] >= 0) ? LD(Jc[w0[k]]) : 0;
+                int nopen = 0;
+#pragma unroll
+                for (int k = 0; k < JU; ++k) {
+                    open[k] = false;
+                    if (!ok[k]) continue;
+                    int nv;
+                    if (w0[k] < 0) nv = w0[k];
+                    else if (w2[k] < 0) nv = w2[k];
+                    else if (w2[k] == w0[k]) nv = ~w0[k];
+                    else {
+                        nv = w2[k];
+                        open[k] = true;
+                        ++nopen;
+                    }
+                    Jn[v[k]] = nv;
+                    if (!open[k]) Jc[v[k]] = nv;
+                }
+                long long q = block_reserve(&ctl->cnt[(r + 1) % 3], nopen);
+#pragma unroll
+                for (int k = 0; k < JU; ++k)
+                    if (open[k]) out[q++] = v[k];
             }
             if (!grid_barrier(ctl, &ctl->bar[0])) return;
             int *t = Jc; Jc = Jn; Jn = t;
@@ -749,13 +765,31 @@ __global__ void k_mark(Ctl *ctl, const int *act, int *J0, int *J1, unsigned char
         }
         if (gtid() == 0) ctl->flag[(r + 1) % 3] = 0;
         bool more = false;
-        for (long long i = gtid(); i < na; i += gstride()) {
-            int v = act[i];
-            int w = LD(Jc[v]);
-            if (LD(mark[v])) mark[w] = 1;
-            int w2 = LD(Jc[w]);
-            Jn[v] = w2;
-            more |= parent[w2] != w2;
+        const long long S = gstride();
+        for (long long base = gtid(); base < na; base += S * JU) {
+            int v[JU], w[JU], w2[JU];
+            bool ok[JU];
+            unsigned char mk[JU];
+#pragma unroll
+            for (int k = 0; k < JU; ++k) {
+                long long i = base + k * S;
+                ok[k] = i < na;
+                v[k] = ok[k] ? act[i] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < JU; ++k) {
+                w[k] = ok[k] ? LD(Jc[v[k]]) : 0;
+                mk[k] = ok[k] ? LD(mark[v[k]]) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < JU; ++k) w2[k] = ok[k] ? LD(Jc[w[k]]) : 0;
+#pragma unroll
+            for (int k = 0; k < JU; ++k) {
+                if (!ok[k]) continue;
+                if (mk[k]) mark[w[k]] = 1;
+                Jn[v[k]] = w2[k];
+                more |= parent[w2[k]] != w2[k];
+            }
         }
         if (__syncthreads_or(more) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
         if (!grid_barrier(ctl, &ctl->bar[3])) return;
