@@ -225,6 +225,33 @@ __device__ __forceinline__ long long block_reserve(u64 *ctr, int cnt) {
     return r;
 }
 
+// Block-aggregated reservation for four separate slabs: thread t has
+// flags f[0..3] (item k of thread t lies in input slab k); the output keeps
+// slab order and, within a slab, thread order, so a compacted list keeps the
+// order of its input.  One block scan of the four counts packed in 16-bit
+// fields (a block has at most 1024 threads) and one atomicAdd per block.
+// Returns the output slot of item k in slot[k] (-1 when its flag is 0).
+__device__ __forceinline__ void block_reserve4(u64 *ctr, const bool f[4], long long slot[4]) {
+    __shared__ u64 s_rb4;
+    long long packed = (long long)f[0] | ((long long)f[1] << 16) | ((long long)f[2] << 32) | ((long long)f[3] << 48);
+    long long tot;
+    long long pre = block_excl_scan_ll(packed, &tot);
+    long long t[4], p[4];
+    for (int k = 0; k < 4; ++k) {
+        t[k] = (tot >> (16 * k)) & 0xFFFF;
+        p[k] = (pre >> (16 * k)) & 0xFFFF;
+    }
+    long long all = t[0] + t[1] + t[2] + t[3];
+    if (threadIdx.x == 0) s_rb4 = all ? atomicAdd(ctr, (u64)all) : 0;
+    __syncthreads();
+    long long base = (long long)s_rb4, off = 0;
+    for (int k = 0; k < 4; ++k) {
+        slot[k] = f[k] ? base + off + p[k] : -1;
+        off += t[k];
+    }
+    __syncthreads();
+}
+
 // 64-bit minimum over a group of lanes (mask from __match_any_sync).
 __device__ __forceinline__ u64 group_min_u64(unsigned grp, u64 k) {
     unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;

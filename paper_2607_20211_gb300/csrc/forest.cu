@@ -168,10 +168,12 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
                     Jn[v[k]] = nv;
                     if (!open[k]) Jc[v[k]] = nv;
                 }
-                long long q = block_reserve(&ctl->cnt[(r + 1) % 3], nopen);
+                (void)nopen;
+                long long q[JU];
+                block_reserve4(&ctl->cnt[(r + 1) % 3], open, q);
 #pragma unroll
                 for (int k = 0; k < JU; ++k)
-                    if (open[k]) out[q++] = v[k];
+                    if (open[k]) out[q[k]] = v[k];
             }
             if (!grid_barrier(ctl, &ctl->bar[0])) return;
             int *t = Jc; Jc = Jn; Jn = t;
