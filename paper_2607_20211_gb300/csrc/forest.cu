@@ -186,11 +186,12 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
             }
             return;
         }
-        // final pass: representatives, piece weights (sum of row lengths + 1
-        // per vertex; weights of piece roots were zeroed at the cut), and a
+        // final pass: representatives, piece weights (vertex counts; the
+        // weight slots of piece roots were zeroed at the cut) and a
         // provisional list of rows to scan: every vertex outside its tree's
-        // root piece.  The dominant piece of the block is summed in shared
-        // memory (one global atomic per block for it).
+        // root piece (only those read their row length).  JU vertices per
+        // thread and iteration; the dominant piece of the block is counted
+        // in shared memory (one global atomic per block for it).
         __shared__ int s_p;
         __shared__ unsigned s_sum;
         if (threadIdx.x == 0) {
@@ -198,35 +199,56 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
             s_sum = 0;
         }
         __syncthreads();
-        for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += gstride()) {
-            long long i = base + threadIdx.x;
-            bool valid = i < cnt, scan = false;
-            int v = 0, p = 0;
-            long long len = 0;
-            if (valid) {
-                v = A[i];
-                p = ~LD(Jc[v]);
-                rep[v] = p;
-                long long cap = g.off[v + 1] - g.off[v];
-                long long used = g.used[v];
-                len = used < cap ? used : cap;
-                scan = p != rold[v] && len > 0;
+        const long long S = gstride();
+        for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += S * JU) {
+            int v[JU], p[JU], ro[JU];
+            bool ok[JU], scan[JU];
+            long long len[JU];
+#pragma unroll
+            for (int k = 0; k < JU; ++k) {
+                long long i = base + k * S + threadIdx.x;
+                ok[k] = i < cnt;
+                v[k] = ok[k] ? A[i] : 0;
             }
-            unsigned vm = __ballot_sync(0xffffffffu, valid);
-            if (valid) {
-                unsigned grp = __match_any_sync(vm, p);
-                unsigned tot = __reduce_add_sync(grp, (unsigned)len + 1u);
-                if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
-                    if (*(volatile int *)&s_p == -1) atomicCAS(&s_p, -1, p);
-                    if (*(volatile int *)&s_p == p) atomicAdd(&s_sum, tot);
-                    else atomicAdd(&w[p], tot);
+#pragma unroll
+            for (int k = 0; k < JU; ++k) {
+                p[k] = ok[k] ? ~LD(Jc[v[k]]) : 0;
+                ro[k] = ok[k] ? rold[v[k]] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < JU; ++k) {
+                scan[k] = false;
+                len[k] = 0;
+                if (!ok[k]) continue;
+                rep[v[k]] = p[k];
+                if (p[k] != ro[k]) {
+                    long long cap = g.off[v[k] + 1] - g.off[v[k]];
+                    long long used = g.used[v[k]];
+                    len[k] = used < cap ? used : cap;
+                    scan[k] = len[k] > 0;
                 }
             }
-            long long q = block_append(&ctl->ndet, scan);
-            if (scan) {
-                D[q] = v;
-                roff[q] = len;
+#pragma unroll
+            for (int k = 0; k < JU; ++k) {
+                unsigned vm = __ballot_sync(0xffffffffu, ok[k]);
+                if (ok[k]) {
+                    unsigned grp = __match_any_sync(vm, p[k]);
+                    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
+                        unsigned tot = (unsigned)__popc(grp);
+                        if (*(volatile int *)&s_p == -1) atomicCAS(&s_p, -1, p[k]);
+                        if (*(volatile int *)&s_p == p[k]) atomicAdd(&s_sum, tot);
+                        else atomicAdd(&w[p[k]], tot);
+                    }
+                }
             }
+            long long q[JU];
+            block_reserve4(&ctl->ndet, scan, q);
+#pragma unroll
+            for (int k = 0; k < JU; ++k)
+                if (scan[k]) {
+                    D[q[k]] = v[k];
+                    roff[q[k]] = len[k];
+                }
         }
         __syncthreads();
         if (threadIdx.x == 0 && s_p != -1) atomicAdd(&w[s_p], s_sum);
@@ -244,11 +266,7 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
         if (!grid_barrier(ctl, &ctl->bar[0])) return;
         for (long long i = gtid(); i < cnt; i += gstride()) {
             int v = A[i];
-            int p = LD(rep[v]);
-            long long cap = g.off[v + 1] - g.off[v];
-            long long used = g.used[v];
-            unsigned d = (unsigned)(used < cap ? used : cap) + 1u;
-            atomicAdd(&w[p], d);
+            atomicAdd(&w[LD(rep[v])], 1u);
         }
     }
     if (!grid_barrier(ctl, &ctl->bar[0])) return;
