@@ -23,6 +23,10 @@
 #define ORIENT_THREADS 1024
 // independent items per thread and iteration in the pointer-doubling rounds
 #define JU 4
+// a detached piece is left out of the cross-edge scan instead of its tree's
+// root piece only if it has this many more vertices (the swap costs a full
+// pass over the affected list)
+#define HEAVY_SWAP_MIN 4096
 
 #define GS_LOOP(i, n) \
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)(n); \
@@ -284,7 +288,9 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
         unsigned lmax = __reduce_max_sync(grp, hi == hmax ? lo : 0u);
         if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
             atomicMax(&heavy[r], ((u64)hmax << 32) | lmax);
-            atomicMax(&heavy[r], ((u64)LD(w[r]) << 32) | (unsigned)r);
+            // the root piece stays the piece left out unless a detached
+            // piece outweighs it by HEAVY_SWAP_MIN vertices
+            atomicMax(&heavy[r], ((u64)(LD(w[r]) + HEAVY_SWAP_MIN) << 32) | (unsigned)r);
         }
     }
     if (!grid_barrier(ctl, &ctl->bar[0])) return;
@@ -515,7 +521,11 @@ __global__ void __launch_bounds__(ORIENT_THREADS) k_orient(Ctl *ctl, OrientArgs 
         u64 k = a.er[j >> 1];
         int p = a.rep[(j & 1) ? khi(k) : klo(k)];
         a.ep[j] = p;
-        bool first = atomicExch(&a.pstamp[p], ep) != ep;
+        // one lane per piece among the warp's lanes claims it (a piece such
+        // as the giant one is an endpoint of most of the batch's edges)
+        unsigned grp = __match_any_sync(__activemask(), p);
+        bool lead = (int)(threadIdx.x & 31) == __ffs(grp) - 1;
+        bool first = lead && __ldcg(&a.pstamp[p]) != ep && atomicExch(&a.pstamp[p], ep) != ep;
         long long id = agg_append(&ctl->npc, first);
         if (first) {
             a.pidx[p] = (int)id;
