@@ -83,8 +83,10 @@ enum {
     /* drsf_create checks on the device that parent is a rooted spanning
      * forest of G and fails with DRSF_ENOT_FOREST otherwise (synchronises). */
     DRSF_VALIDATE = 2u,
-    /* Mark the reversed paths with the Euler-tour intervals of the re-rooted
-     * trees (Algorithm 3) instead of pointer-doubling marks; same result. */
+    /* Reverse every re-rooted tree's path through the Euler-tour intervals
+     * of the re-rooted trees (Algorithm 3).  Default: paths of up to 64
+     * edges are reversed by one walking thread each, longer ones through
+     * pointer-doubling marks.  Same result. */
     DRSF_EULER_REVERSAL = 4u
 };
 
@@ -98,13 +100,18 @@ typedef struct {
     int64_t tree_cut;      /* deleted edges that were tree edges (delete) */
     int64_t affected;      /* vertices of trees that lost an edge (delete) */
     int64_t detached;      /* rows scanned for cross edges: vertices of cut trees
-                              outside the heaviest piece of their tree (delete) */
+                              outside the piece left out of the scan, the root
+                              piece unless a detached piece has 4096 more
+                              vertices, then the heaviest piece (delete) */
     int64_t scanned;       /* adjacency entries scanned for cross edges */
     int64_t candidates;    /* cross edges found */
     int64_t hook_rounds;   /* hook-and-compress rounds */
     int64_t replacement;   /* replacement edges |E_r| */
     int64_t rank_rounds;   /* list-ranking rounds of the Euler tour */
-    int64_t active;        /* vertices in re-rooted trees (path reversal) */
+    int64_t active;        /* vertices of the re-rooted trees whose path goes
+                              through the marks: trees whose path is longer
+                              than 64 edges (all re-rooted trees with
+                              DRSF_EULER_REVERSAL) */
     int64_t reversed;      /* vertices whose parent pointer was reversed */
     int64_t mark_rounds;   /* pointer-doubling rounds of the path reversal */
     int64_t jump_rounds;   /* pointer-jumping rounds for representatives */

@@ -53,10 +53,12 @@ struct drsf_ctx {
     int *att_x = nullptr, *newrep = nullptr, *A = nullptr, *act = nullptr, *pold = nullptr, *D = nullptr;
     int *chx = nullptr, *chy = nullptr;
     unsigned *aff_ep = nullptr, *cut_ep = nullptr, *pstamp = nullptr, *att_ep = nullptr, *rep_ep = nullptr;
+    unsigned *long_ep = nullptr;
     u64 *best0 = nullptr, *best1 = nullptr, *er = nullptr, *heavy = nullptr;
     int *rold = nullptr, *cdeg = nullptr, *xlist = nullptr, *aidx = nullptr, *aroot = nullptr;
     int *oep = nullptr, *oeid = nullptr, *oeroot = nullptr;
-    long long *roff = nullptr;
+    long long *roff = nullptr, *rbase = nullptr;
+    int2 *rmeta = nullptr;
     unsigned char *lf = nullptr;
     unsigned *wgt = nullptr;
     PairTable pt{};
@@ -111,6 +113,8 @@ enum {
 static const char *kPhaseNames[DRSF_NUM_PHASES] = {
     "begin", "ins_claim", "ins_place", "del_claim", "affected", "jump", "scan", "hook", "orient", "active",
     "mark", "reverse"};
+
+static RowList rows(drsf_ctx *h) { return RowList{h->D, h->roff, h->rbase, h->rmeta}; }
 
 static void prof_begin(drsf_ctx *h, int phase, cudaStream_t s) {
     if (!h->prof_on || 2 * (h->prof_used + 1) > h->prof_ev.size()) return;
@@ -419,12 +423,15 @@ static drsf_status alloc_work(drsf_ctx *h, cudaStream_t s) {
     CKA(halloc(h, &h->cut_ep, n, s));
     CKA(halloc(h, &h->pstamp, n, s));
     CKA(halloc(h, &h->att_ep, n, s));
+    CKA(halloc(h, &h->long_ep, n, s));
     CKA(halloc(h, &h->rep_ep, n, s));
     CKA(halloc(h, &h->best0, n, s));
     CKA(halloc(h, &h->best1, n, s));
     CKA(halloc(h, &h->heavy, n, s));
     CKA(halloc(h, &h->rold, n, s));
     CKA(halloc(h, &h->roff, n + 1, s));
+    CKA(halloc(h, &h->rbase, n, s));
+    CKA(halloc(h, &h->rmeta, n, s));
     CKA(halloc(h, &h->xlist, n, s));
     CKA(halloc(h, &h->aidx, n, s));
     CKA(halloc(h, &h->aroot, n, s));
@@ -447,7 +454,7 @@ static drsf_status alloc_work(drsf_ctx *h, cudaStream_t s) {
     CKA(halloc(h, &h->nx1, 2 * n + 2, s));
     CKA(halloc(h, &h->bsum, 8192, s));
     CKA(halloc(h, &h->ctl, 1, s));
-    unsigned *eps[] = {h->aff_ep, h->cut_ep, h->pstamp, h->att_ep, h->rep_ep};
+    unsigned *eps[] = {h->aff_ep, h->cut_ep, h->pstamp, h->att_ep, h->rep_ep, h->long_ep};
     for (unsigned *e : eps) CK(cudaMemsetAsync(e, 0, n * sizeof(unsigned), s));
     CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
     return DRSF_OK;
@@ -500,8 +507,8 @@ static drsf_status create_impl(drsf_ctx *h, const int32_t *edges, int64_t m, con
     // representatives of F by pointer jumping over all vertices
     CK(launch_copy_parent(n, h->parent, h->J0, s));
     Csr g0{h->off, h->used, h->col};
-    CK(launch_jump(h->dev, nullptr, 0, n, h->ctl, h->J0, h->J1, h->rep, h->D, 0, h->rold, h->wgt, h->heavy, g0,
-                   h->roff, h->bsum, h->jump_sync, h->act, h->xlist, h->cutlist, s));
+    CK(launch_jump(h->dev, nullptr, 0, n, h->ctl, h->J0, h->J1, h->rep, rows(h), 0, h->rold, h->wgt, h->heavy, g0,
+                   h->bsum, h->jump_sync, h->act, h->xlist, h->cutlist, s));
     Ctl c{};
     CK(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -614,12 +621,11 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
                               ctl, s));
         prof_end(h, PH_AFF, 1, s);
         prof_begin(h, PH_JUMP, s);
-        CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->J0, h->J1, h->rep, h->D, 1, h->rold, h->wgt, h->heavy, g,
-                       h->roff, h->bsum, h->jump_sync, h->act, h->xlist, h->cutlist, s));
+        CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->J0, h->J1, h->rep, rows(h), 1, h->rold, h->wgt, h->heavy, g,
+                       h->bsum, h->jump_sync, h->act, h->xlist, h->cutlist, s));
         prof_end(h, PH_JUMP, 1, s);
         prof_begin(h, PH_SCAN, s);
-        CK(launch_scan_rows(h->dev, h->D, h->roff, ctl, g, h->rep, h->rold, h->heavy, h->pt, h->ck[0], h->ca[0],
-                            h->cb[0], h->cand_cap, s));
+        CK(launch_scan_rows(h->dev, rows(h), ctl, g, h->rep, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
         CK(launch_scan_ovf(h->dev, h->ovf, ctl, h->rep, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
         CK(launch_pairs_compact(h->dev, ctl, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
         prof_end(h, PH_SCAN, 3, s);
@@ -660,16 +666,26 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
     prof_begin(h, PH_ORIENT, s);
     CK(launch_orient(h->dev, ctl, oa, s));
     prof_end(h, PH_ORIENT, 1, s);
+    // Path reversal: by default short paths are reversed by walking and only
+    // the pieces with long paths go through the marks; the Euler-tour
+    // variant (Algorithm 3) takes every re-rooted piece.
+    const bool euler = (h->flags & DRSF_EULER_REVERSAL) != 0;
+    if (!euler) {
+        prof_begin(h, PH_REVERSE, s);
+        CK(launch_walk(h->dev, ctl, h->chx, h->chy, h->rep, h->parent, h->long_ep, s));
+        prof_end(h, PH_REVERSE, 1, s);
+    }
+    const unsigned *sel = euler ? h->att_ep : h->long_ep;
     prof_begin(h, PH_ACTIVE, s);
     if (op == DRSF_INSERT)
-        CK(launch_active(h->dev, nullptr, 0, h->n, ctl, h->rep, h->parent, h->att_ep, h->att_x, h->rep_ep,
-                         h->newrep, h->act, h->pold, h->J0, h->mark, h->aidx, h->aroot, s));
-    else
-        CK(launch_active(h->dev, h->A, 1, 0, ctl, h->rep, h->parent, h->att_ep, h->att_x, h->rep_ep, h->newrep,
+        CK(launch_active(h->dev, nullptr, 0, h->n, ctl, h->rep, h->parent, sel, h->att_x, h->rep_ep, h->newrep,
                          h->act, h->pold, h->J0, h->mark, h->aidx, h->aroot, s));
+    else
+        CK(launch_active(h->dev, h->A, 1, 0, ctl, h->rep, h->parent, sel, h->att_x, h->rep_ep, h->newrep, h->act,
+                         h->pold, h->J0, h->mark, h->aidx, h->aroot, s));
     prof_end(h, PH_ACTIVE, 1, s);
     prof_begin(h, PH_MARK, s);
-    if (h->flags & DRSF_EULER_REVERSAL) {
+    if (euler) {
         // Algorithm 3: Euler-tour intervals of the re-rooted pieces
         EtArgs ea{};
         ea.act = h->act;

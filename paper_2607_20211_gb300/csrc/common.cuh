@@ -158,6 +158,19 @@ __device__ __forceinline__ bool pair_min(u64 *pk, u64 *mk, u64 mask, int a, int 
     return false;
 }
 
+// Block-wide sum of per-thread counts added to a counter: one atomic per
+// block.  Every thread of the block must call it.
+__device__ __forceinline__ void block_add(long long *ctr, long long v) {
+    __shared__ unsigned long long s_sum;
+    if (threadIdx.x == 0) s_sum = 0;
+    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_sum, (unsigned long long)v);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_sum) atomicAdd((unsigned long long *)ctr, s_sum);
+    __syncthreads();
+}
+
 // Block-aggregated append: one atomicAdd per block.  Every thread of the
 // block must call it (the loop around it must be block-uniform); the slots
 // of a block are contiguous and ordered by thread index.
@@ -249,6 +262,21 @@ __device__ __forceinline__ void block_reserve4(u64 *ctr, const bool f[4], long l
         slot[k] = f[k] ? base + off + p[k] : -1;
         off += t[k];
     }
+    __syncthreads();
+}
+
+// The same for two slabs.
+__device__ __forceinline__ void block_reserve2(u64 *ctr, const bool f[2], long long slot[2]) {
+    __shared__ u64 s_rb2;
+    long long packed = (long long)f[0] | ((long long)f[1] << 32);
+    long long tot;
+    long long pre = block_excl_scan_ll(packed, &tot);
+    long long t0 = tot & 0xFFFFFFFFll, t1 = tot >> 32;
+    if (threadIdx.x == 0) s_rb2 = t0 + t1 ? atomicAdd(ctr, (u64)(t0 + t1)) : 0;
+    __syncthreads();
+    long long base = (long long)s_rb2;
+    slot[0] = f[0] ? base + (pre & 0xFFFFFFFFll) : -1;
+    slot[1] = f[1] ? base + t0 + (pre >> 32) : -1;
     __syncthreads();
 }
 

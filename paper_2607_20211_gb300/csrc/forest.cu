@@ -23,10 +23,35 @@
 #define ORIENT_THREADS 1024
 // independent items per thread and iteration in the pointer-doubling rounds
 #define JU 4
+// the same for the final pass of the jump (more state per item)
+#define JF 2
+// consecutive items per thread in the list-building vertex passes
+#define IPT 4
+// longest path reversed by one walking thread (longer ones: doubling marks)
+#define WALK_MAX 64
+
+// x[k] = a[i0 + k] for k < IPT (i0 a multiple of IPT; a 16-byte aligned):
+// one vector load when all IPT items are in range.
+__device__ __forceinline__ void load_ipt(const int *a, long long i0, long long cnt, int x[IPT]) {
+    if (i0 + IPT <= cnt) {
+        int4 q = *reinterpret_cast<const int4 *>(a + i0);
+        x[0] = q.x;
+        x[1] = q.y;
+        x[2] = q.z;
+        x[3] = q.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) x[k] = i0 + k < cnt ? a[i0 + k] : 0;
+    }
+}
 // a detached piece is left out of the cross-edge scan instead of its tree's
 // root piece only if it has this many more vertices (the swap costs a full
 // pass over the affected list)
 #define HEAVY_SWAP_MIN 4096
+// shared-memory piece-count table of the final jump pass
+#define WT_BITS 6
+#define WT_SLOTS (1 << WT_BITS)
+#define WT_PROBES 8
 
 #define GS_LOOP(i, n) \
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)(n); \
@@ -54,20 +79,34 @@ __global__ void k_begin(Ctl *ctl, int op, long long len) {
 
 // Delete: list the vertices of every tree that lost a tree edge (its old
 // root was stamped by the cut) and seed J0 = parent (the cut forest F^).
+// Each thread takes IPT consecutive vertices per iteration (one vector load
+// of rep, IPT gathers in flight) and the block reserves its list slots with
+// one atomic; the list stays in vertex order.
 __global__ void k_aff_collect(int n, const int *rep, const unsigned *aff_ep, const int *parent, int *J0, int *A,
                               int *rold, unsigned *w, u64 *heavy, Ctl *ctl) {
     if (*(volatile int *)&ctl->skip) return;
     unsigned ep = ctl->epoch;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
-        long long v = base + threadIdx.x;
-        int r = v < n ? rep[v] : 0;
-        bool in = v < n && aff_ep[r] == ep;
-        long long p = block_append(&ctl->naff, in);
-        if (in) {
-            A[p] = (int)v;
+    const long long step = (long long)gridDim.x * blockDim.x * IPT;
+    for (long long b0 = (long long)blockIdx.x * blockDim.x * IPT; b0 < n; b0 += step) {
+        const long long v0 = b0 + (long long)threadIdx.x * IPT;
+        int r[IPT];
+        bool in[IPT];
+        load_ipt(rep, v0, n, r);
+        int c = 0;
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            in[k] = v0 + k < n && aff_ep[r[k]] == ep;
+            c += in[k];
+        }
+        long long p = block_reserve(&ctl->naff, c);
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            if (!in[k]) continue;
+            const int v = (int)(v0 + k);
+            A[p++] = v;
             J0[v] = parent[v];
-            rold[v] = r;
-            if (r == (int)v) {   // the old root: piece-weight and heaviest-piece slots
+            rold[v] = r[k];
+            if (r[k] == v) {   // the old root: piece-weight and heaviest-piece slots
                 w[v] = 0;
                 heavy[v] = 0;
             }
@@ -96,17 +135,38 @@ __device__ __forceinline__ int find_halving(int *J, int v, Ctl *ctl) {
     return x;
 }
 
+// Adds cnt to the weight of piece p through the block's shared table
+// (open addressing, WT_PROBES probes), or to w[p] when no slot is free.
+__device__ __forceinline__ void piece_count(int *s_wk, unsigned *s_wc, unsigned *w, int p, unsigned cnt) {
+    unsigned h = ((unsigned)p * 0x9E3779B1u) >> (32 - WT_BITS);
+    for (int pr = 0; pr < WT_PROBES; ++pr) {
+        int key = *(volatile int *)&s_wk[h];
+        if (key == -1) key = atomicCAS(&s_wk[h], -1, p);
+        if (key == -1 || key == p) {
+            atomicAdd(&s_wc[h], cnt);
+            return;
+        }
+        h = (h + 1) & (WT_SLOTS - 1);
+    }
+    atomicAdd(&w[p], cnt);
+}
+
 // Representatives (Algorithm 1, parallel pointer jumping) of the listed
 // vertices: rep[v] = root of v in F^ (J starts as a copy of parent).
 // Delete mode (1) then chooses the rows to scan for cross edges: every cross
 // edge joins two pieces of one old tree, so scanning all pieces but one per
-// tree finds each of them; the piece left out is the heaviest (largest sum
-// of row lengths), which keeps the scan small when a cut near the root
-// detaches most of a tree.  The listed rows D get an exclusive prefix sum of
-// their lengths in roff (roff[ndet] = total) for the load-balanced scan.
-__global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1, int *rep,
-                       int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g, long long *roff,
-                       long long *bsum, int sync_rounds, int *X, int *Y, const int *cuts) {
+// tree finds each of them.  The piece left out is the root piece, unless a
+// detached piece has HEAVY_SWAP_MIN more vertices (a cut near the root that
+// detaches most of a tree): then the heaviest piece.  The listed rows get an
+// exclusive prefix sum of their lengths in roff (roff[ndet] = total), their
+// CSR start and their (piece, piece left out) for the load-balanced scan.
+// (6 blocks of BLK threads per SM: the rounds are latency-bound)
+__global__ void __launch_bounds__(BLK, 6)
+    k_jump(const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1, int *rep, RowList rl, int mode,
+           const int *rold, unsigned *w, u64 *heavy, Csr g, long long *bsum, int sync_rounds, int *X, int *Y,
+           const int *cuts) {
+    int *const D = rl.D;
+    long long *const roff = rl.roff;
     if (*(volatile int *)&ctl->skip) return;
     long long cnt = use_list ? (long long)ctl->naff : cnt_static;
     if (sync_rounds) {
@@ -194,68 +254,69 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
         // weight slots of piece roots were zeroed at the cut) and a
         // provisional list of rows to scan: every vertex outside its tree's
         // root piece (only those read their row length).  JU vertices per
-        // thread and iteration; the dominant piece of the block is counted
-        // in shared memory (one global atomic per block for it).
-        __shared__ int s_p;
-        __shared__ unsigned s_sum;
-        if (threadIdx.x == 0) {
-            s_p = -1;
-            s_sum = 0;
+        // thread and iteration.  Piece counts go to a small open-addressing
+        // table in shared memory (one global atomic per piece and block at
+        // the end; a large piece spans many blocks), or straight to global
+        // memory when the table has no slot.
+        __shared__ int s_wk[WT_SLOTS];
+        __shared__ unsigned s_wc[WT_SLOTS];
+        for (int t = threadIdx.x; t < WT_SLOTS; t += blockDim.x) {
+            s_wk[t] = -1;
+            s_wc[t] = 0;
         }
         __syncthreads();
         const long long S = gstride();
-        for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += S * JU) {
-            int v[JU], p[JU], ro[JU];
-            bool ok[JU], scan[JU];
-            long long len[JU];
+        for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += S * JF) {
+            int v[JF], p[JF], ro[JF], len[JF];
+            bool ok[JF], scan[JF];
 #pragma unroll
-            for (int k = 0; k < JU; ++k) {
+            for (int k = 0; k < JF; ++k) {
                 long long i = base + k * S + threadIdx.x;
                 ok[k] = i < cnt;
                 v[k] = ok[k] ? A[i] : 0;
             }
 #pragma unroll
-            for (int k = 0; k < JU; ++k) {
+            for (int k = 0; k < JF; ++k) {
                 p[k] = ok[k] ? ~LD(Jc[v[k]]) : 0;
                 ro[k] = ok[k] ? rold[v[k]] : 0;
             }
 #pragma unroll
-            for (int k = 0; k < JU; ++k) {
+            for (int k = 0; k < JF; ++k) {
                 scan[k] = false;
                 len[k] = 0;
                 if (!ok[k]) continue;
                 rep[v[k]] = p[k];
                 if (p[k] != ro[k]) {
-                    long long cap = g.off[v[k] + 1] - g.off[v[k]];
-                    long long used = g.used[v[k]];
+                    int cap = (int)(g.off[v[k] + 1] - g.off[v[k]]);
+                    int used = g.used[v[k]];
                     len[k] = used < cap ? used : cap;
                     scan[k] = len[k] > 0;
                 }
             }
 #pragma unroll
-            for (int k = 0; k < JU; ++k) {
+            for (int k = 0; k < JF; ++k) {
                 unsigned vm = __ballot_sync(0xffffffffu, ok[k]);
                 if (ok[k]) {
                     unsigned grp = __match_any_sync(vm, p[k]);
                     if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
-                        unsigned tot = (unsigned)__popc(grp);
-                        if (*(volatile int *)&s_p == -1) atomicCAS(&s_p, -1, p[k]);
-                        if (*(volatile int *)&s_p == p[k]) atomicAdd(&s_sum, tot);
-                        else atomicAdd(&w[p[k]], tot);
+                        piece_count(s_wk, s_wc, w, p[k], (unsigned)__popc(grp));
                     }
                 }
             }
-            long long q[JU];
-            block_reserve4(&ctl->ndet, scan, q);
+            long long q[JF];
+            block_reserve2(&ctl->ndet, scan, q);
 #pragma unroll
-            for (int k = 0; k < JU; ++k)
+            for (int k = 0; k < JF; ++k)
                 if (scan[k]) {
                     D[q[k]] = v[k];
                     roff[q[k]] = len[k];
+                    rl.base[q[k]] = g.off[v[k]];
+                    rl.meta[q[k]] = make_int2(p[k], ro[k]);
                 }
         }
         __syncthreads();
-        if (threadIdx.x == 0 && s_p != -1) atomicAdd(&w[s_p], s_sum);
+        for (int t = threadIdx.x; t < WT_SLOTS; t += blockDim.x)
+            if (s_wk[t] != -1) atomicAdd(&w[s_wk[t]], s_wc[t]);
     } else {
         // J[v] may later be overwritten by another walk's halving step with
         // a non-root ancestor; rep[v] takes this thread's own result.
@@ -314,20 +375,23 @@ __global__ void k_jump(const int *A, int use_list, long long cnt_static, Ctl *ct
         for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += gstride()) {
             long long i = base + threadIdx.x;
             bool scan = false;
-            int v = 0;
+            int v = 0, hp = 0, pv = 0;
             long long len = 0;
             if (i < cnt) {
                 v = A[i];
-                int hp = (int)(unsigned)LD(heavy[rold[v]]);
+                hp = (int)(unsigned)LD(heavy[rold[v]]);
                 long long cap = g.off[v + 1] - g.off[v];
                 long long used = g.used[v];
                 len = used < cap ? used : cap;
-                scan = LD(rep[v]) != hp && len > 0;
+                pv = LD(rep[v]);
+                scan = pv != hp && len > 0;
             }
             long long q = block_append(&ctl->ndet, scan);
             if (scan) {
                 D[q] = v;
                 roff[q] = len;
+                rl.base[q] = g.off[v];
+                rl.meta[q] = make_int2(pv, hp);
             }
         }
     }
@@ -741,39 +805,102 @@ __global__ void __launch_bounds__(ORIENT_THREADS) k_orient(Ctl *ctl, OrientArgs 
     }
 }
 
+// Path reversal by walking (ReversePaths, Algorithm 1), one thread per
+// oriented replacement edge x -> y: the path x = v0, v1 = parent[v0], ...,
+// vL (the piece root) is reversed in place while it is walked (parent[v_j]
+// <- v_{j-1}, parent[v0] <- y).  Each child piece has exactly one oriented
+// edge and pieces are disjoint, so the walks never touch the same vertex.
+// A walk that has not met its root after WALK_MAX steps restores the part
+// it reversed and stamps its piece in long_ep: such pieces are reversed by
+// the pointer-doubling marks instead.
+__global__ void k_walk(Ctl *ctl, const int *chx, const int *chy, const int *rep, int *parent, unsigned *long_ep) {
+    if (*(volatile int *)&ctl->skip) return;
+    const unsigned ep = ctl->epoch;
+    const long long ner = (long long)ctl->ner;
+    long long rev = 0;
+    GS_LOOP(i, ner) {
+        const int x = chx[i];
+        int prev = chy[i], cur = x, steps = 0;
+        bool done = false;
+        for (; steps < WALK_MAX; ++steps) {
+            int nxt = parent[cur];
+            parent[cur] = prev;
+            if (nxt == cur) {
+                done = true;
+                break;
+            }
+            prev = cur;
+            cur = nxt;
+        }
+        if (done) {
+            rev += steps;   // the path's vertices below the root
+        } else {
+            // v0 .. v_{WALK_MAX-1} reversed, cur = v_WALK_MAX untouched
+            int up = cur, v = prev;
+            for (int t = 0; t < WALK_MAX; ++t) {
+                int nv = parent[v];
+                parent[v] = up;
+                up = v;
+                v = nv;
+            }
+            long_ep[rep[x]] = ep;
+        }
+    }
+    if (rev) atomicAdd((u64 *)&ctl->reversed, (u64)rev);
+}
+
 // Path-reversal set-up fused with the representative refresh: a vertex of a
 // piece that is re-rooted at an attach point x != its root is active (its
 // old parent is saved, J0 seeded, x marked); every vertex of a merged piece
 // takes the super-tree's root as its new rep.
 __global__ void k_active(const int *L, int use_list, long long cnt_static, Ctl *ctl, int *rep, const int *parent,
-                         const unsigned *att_ep, const int *att_x, const unsigned *rep_ep, const int *newrep,
+                         const unsigned *sel_ep, const int *att_x, const unsigned *rep_ep, const int *newrep,
                          int *act, int *pold, int *J0, unsigned char *mark, int *aidx, int *aroot) {
     if (*(volatile int *)&ctl->skip) return;
     unsigned ep = ctl->epoch;
     long long cnt = use_list ? (long long)ctl->naff : cnt_static;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += (long long)gridDim.x * blockDim.x) {
-        long long i = base + threadIdx.x;
-        bool on = false;
-        int v = 0, p = 0, x = -1;
-        if (i < cnt) {
-            v = use_list ? L[i] : (int)i;
-            p = rep[v];
-            if (att_ep[p] == ep) {
-                x = att_x[p];
-                on = x != p;
+    // IPT consecutive items per thread and iteration, one slot reservation
+    // per block (as in k_aff_collect)
+    const long long step = (long long)gridDim.x * blockDim.x * IPT;
+    for (long long b0 = (long long)blockIdx.x * blockDim.x * IPT; b0 < cnt; b0 += step) {
+        const long long i0 = b0 + (long long)threadIdx.x * IPT;
+        int v[IPT], p[IPT], x[IPT];
+        bool on[IPT];
+        if (use_list) {
+            load_ipt(L, i0, cnt, v);
+        } else {
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) v[k] = (int)(i0 + k);
+        }
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) p[k] = i0 + k < cnt ? rep[v[k]] : 0;
+        int c = 0;
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            on[k] = false;
+            x[k] = -1;
+            if (i0 + k < cnt && sel_ep[p[k]] == ep) {
+                x[k] = att_x[p[k]];
+                on[k] = x[k] != p[k];
             }
+            c += on[k];
         }
-        long long q = block_append(&ctl->nact, on);
-        if (on) {
-            int pv = parent[v];
-            act[q] = v;
-            pold[q] = pv;
-            J0[v] = pv;
-            mark[v] = v == x;
-            aidx[v] = (int)q;   // dense index (Euler-tour marks)
-            aroot[q] = p;       // the piece root
+        long long q = block_reserve(&ctl->nact, c);
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            if (i0 + k >= cnt) continue;
+            if (on[k]) {
+                int pv = parent[v[k]];
+                act[q] = v[k];
+                pold[q] = pv;
+                J0[v[k]] = pv;
+                mark[v[k]] = v[k] == x[k];
+                aidx[v[k]] = (int)q;   // dense index (Euler-tour marks)
+                aroot[q] = p[k];       // the piece root
+                ++q;
+            }
+            if (rep_ep[p[k]] == ep) rep[v[k]] = newrep[p[k]];
         }
-        if (i < cnt && rep_ep[p] == ep) rep[v] = newrep[p];
     }
 }
 
@@ -907,7 +1034,7 @@ cudaError_t launch_begin(Ctl *ctl, int op, long long len, cudaStream_t s) {
 }
 cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, const int *parent,
                                int *J0, int *A, int *rold, unsigned *w, u64 *heavy, Ctl *ctl, cudaStream_t s) {
-    k_aff_collect<<<gsz(n), BLK, 0, s>>>(n, rep, aff_ep, parent, J0, A, rold, w, heavy, ctl);
+    k_aff_collect<<<gsz((n + IPT - 1) / IPT), BLK, 0, s>>>(n, rep, aff_ep, parent, J0, A, rold, w, heavy, ctl);
     (void)d;
     return cudaGetLastError();
 }
@@ -916,13 +1043,11 @@ cudaError_t launch_copy_parent(int n, const int *parent, int *J0, cudaStream_t s
     return cudaGetLastError();
 }
 cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1,
-                        int *rep, int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g,
-                        long long *roff, long long *bsum, int sync_rounds, int *X, int *Y, const int *cuts,
-                        cudaStream_t s) {
+                        int *rep, RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g,
+                        long long *bsum, int sync_rounds, int *X, int *Y, const int *cuts, cudaStream_t s) {
     void *args[] = {(void *)&A, (void *)&use_list, (void *)&cnt_static, (void *)&ctl, (void *)&J, (void *)&J1,
-                    (void *)&rep, (void *)&D, (void *)&mode, (void *)&rold, (void *)&w, (void *)&heavy,
-                    (void *)&g, (void *)&roff, (void *)&bsum, (void *)&sync_rounds, (void *)&X, (void *)&Y,
-                    (void *)&cuts};
+                    (void *)&rep, (void *)&rl, (void *)&mode, (void *)&rold, (void *)&w, (void *)&heavy,
+                    (void *)&g, (void *)&bsum, (void *)&sync_rounds, (void *)&X, (void *)&Y, (void *)&cuts};
     return cudaLaunchCooperativeKernel((const void *)k_jump, d.coop_jump, BLK, args, 0, s);
 }
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
@@ -936,12 +1061,17 @@ cudaError_t launch_orient(const Dev &d, Ctl *ctl, OrientArgs a, cudaStream_t s) 
     return cudaLaunchCooperativeKernel((const void *)k_orient, d.coop_orient, ORIENT_THREADS, args,
                                        ORIENT_SMEM_BYTES, s);
 }
+cudaError_t launch_walk(const Dev &d, Ctl *ctl, const int *chx, const int *chy, const int *rep, int *parent,
+                        unsigned *long_ep, cudaStream_t s) {
+    k_walk<<<d.grid, BLK, 0, s>>>(ctl, chx, chy, rep, parent, long_ep);
+    return cudaGetLastError();
+}
 cudaError_t launch_active(const Dev &d, const int *L, int use_list, long long cnt_static, Ctl *ctl, int *rep,
-                          const int *parent, const unsigned *att_ep, const int *att_x, const unsigned *rep_ep,
+                          const int *parent, const unsigned *sel_ep, const int *att_x, const unsigned *rep_ep,
                           const int *newrep, int *act, int *pold, int *J0, unsigned char *mark, int *aidx,
                           int *aroot, cudaStream_t s) {
-    unsigned g = use_list ? d.grid : gsz(cnt_static);
-    k_active<<<g, BLK, 0, s>>>(L, use_list, cnt_static, ctl, rep, parent, att_ep, att_x, rep_ep, newrep, act,
+    unsigned g = use_list ? d.grid : gsz((cnt_static + IPT - 1) / IPT);
+    k_active<<<g, BLK, 0, s>>>(L, use_list, cnt_static, ctl, rep, parent, sel_ep, att_x, rep_ep, newrep, act,
                                 pold, J0, mark, aidx, aroot);
     return cudaGetLastError();
 }

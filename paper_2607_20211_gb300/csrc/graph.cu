@@ -193,26 +193,34 @@ __global__ void k_validate_batch(const int *batch, long long len, int n, Ctl *ct
 // edges already in G; claim an index slot for each new edge.
 __global__ void k_ins_claim(const int *batch, long long len, Index ix, Ctl *ctl, u64 *nkey, u64 *nslot) {
     if (*(volatile int *)&ctl->skip) return;
-    GS_LOOP(i, len) {
-        int u = batch[2 * i], v = batch[2 * i + 1];
-        bool keep = false, drop = false;
+    // block-uniform loop: counters and the list append are aggregated per
+    // block (one atomic per block instead of one per warp)
+    long long loops = 0, drops = 0;
+    for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < len; b0 += (long long)gridDim.x * blockDim.x) {
+        const long long i = b0 + threadIdx.x;
+        bool keep = false;
         u64 key = 0;
         long long s = -1;
-        if (u != v) {
-            key = ekey((uint32_t)u, (uint32_t)v);
-            s = index_claim(ix, key);
-            if (s == LLONG_MIN) atomicOr(&ctl->err, ERR_CAPACITY);
-            keep = s >= 0;
-            drop = !keep;
+        if (i < len) {
+            int u = batch[2 * i], v = batch[2 * i + 1];
+            if (u != v) {
+                key = ekey((uint32_t)u, (uint32_t)v);
+                s = index_claim(ix, key);
+                if (s == LLONG_MIN) atomicOr(&ctl->err, ERR_CAPACITY);
+                keep = s >= 0;
+                drops += !keep;
+            } else {
+                ++loops;
+            }
         }
-        agg_count(&ctl->self_loops, u == v);
-        agg_count(&ctl->dropped, drop);
-        long long p = agg_append(&ctl->nb, keep);
+        long long p = block_append(&ctl->nb, keep);
         if (keep) {
             nkey[p] = key;
             nslot[p] = (u64)s;
         }
     }
+    block_add(&ctl->self_loops, loops);
+    block_add(&ctl->dropped, drops);
 }
 
 // Insert, step 2: append each new edge to both CSR rows (warp-aggregated
@@ -223,35 +231,43 @@ __global__ void k_ins_place(const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, 
                             const int *rep, u64 *ck, int *ca, int *cb, u64 cand_cap) {
     if (*(volatile int *)&ctl->skip) return;
     long long nb = (long long)ctl->nb;
-    GS_LOOP(i, nb) {
-        u64 k = nkey[i];
-        u64 s = nslot[i];
-        uint32_t a = klo(k), b = khi(k);
-        long long oa = g.off[a], ob = g.off[b];
-        long long capa = g.off[a + 1] - oa, capb = g.off[b + 1] - ob;
-        int pa = atomicAdd(&g.used[a], 1), pb = atomicAdd(&g.used[b], 1);
-        bool fa = pa < capa, fb = pb < capb;
-        if (fa && fb) {
-            g.col[oa + pa] = (int)b;
-            g.col[ob + pb] = (int)a;
-            ix.pu[s] = (uint32_t)(oa + pa);
-            ix.pv[s] = (uint32_t)(ob + pb);
-        } else {
-            // the consumed free slot (if any) stays -1
-            u64 o = atomicAdd(&ctl->ovf_count, 1ull);
-            if (o < ovf_cap) {
-                ovf[o] = k;
-                ix.pu[s] = POS_OVF;
-                ix.pv[s] = (uint32_t)o;
+    // block-uniform loop: the candidate append is aggregated per block
+    for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < nb; b0 += (long long)gridDim.x * blockDim.x) {
+        const long long i = b0 + threadIdx.x;
+        bool cross = false;
+        int ra = 0, rb = 0;
+        u64 k = 0;
+        if (i < nb) {
+            k = nkey[i];
+            u64 s = nslot[i];
+            uint32_t a = klo(k), b = khi(k);
+            long long oa = g.off[a], ob = g.off[b];
+            long long capa = g.off[a + 1] - oa, capb = g.off[b + 1] - ob;
+            int pa = atomicAdd(&g.used[a], 1), pb = atomicAdd(&g.used[b], 1);
+            bool fa = pa < capa, fb = pb < capb;
+            if (fa && fb) {
+                g.col[oa + pa] = (int)b;
+                g.col[ob + pb] = (int)a;
+                ix.pu[s] = (uint32_t)(oa + pa);
+                ix.pv[s] = (uint32_t)(ob + pb);
             } else {
-                atomicOr(&ctl->err, ERR_CAPACITY);
+                // the consumed free slot (if any) stays -1
+                u64 o = atomicAdd(&ctl->ovf_count, 1ull);
+                if (o < ovf_cap) {
+                    ovf[o] = k;
+                    ix.pu[s] = POS_OVF;
+                    ix.pv[s] = (uint32_t)o;
+                } else {
+                    atomicOr(&ctl->err, ERR_CAPACITY);
+                }
+                atomicAdd((u64 *)&ctl->overflow_total, 1ull);
+                if (fa || fb) atomicAdd((u64 *)&ctl->ctomb, 1ull);
             }
-            atomicAdd((u64 *)&ctl->overflow_total, 1ull);
-            if (fa || fb) atomicAdd((u64 *)&ctl->ctomb, 1ull);
+            ra = rep[a];
+            rb = rep[b];
+            cross = ra != rb;
         }
-        int ra = rep[a], rb = rep[b];
-        bool cross = ra != rb;
-        long long p = agg_append(&ctl->ncand, cross);
+        long long p = block_append(&ctl->ncand, cross);
         if (cross) {
             if ((u64)p < cand_cap) {
                 ck[p] = k;
@@ -275,69 +291,82 @@ __global__ void k_del_claim(const int *batch, long long len, Index ix, Csr g, u6
                             unsigned *w) {
     if (*(volatile int *)&ctl->skip) return;
     unsigned ep = ctl->epoch;
-    GS_LOOP(i, len) {
-        int u = batch[2 * i], v = batch[2 * i + 1];
-        bool won = false;
+    // block-uniform loop: counters and the cut list append are aggregated
+    // per block (one atomic per block instead of one per warp)
+    long long loops = 0, drops = 0, wins = 0;
+    for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < len; b0 += (long long)gridDim.x * blockDim.x) {
+        const long long i = b0 + threadIdx.x;
         int c = -1;
-        if (u != v) {
-            u64 key = ekey((uint32_t)u, (uint32_t)v);
-            long long s = index_find(ix, key);
-            if (s >= 0) won = atomicCAS(&ix.key[s], key, TOMB_KEY) == key;
-            if (won) {
-                uint32_t pu = ix.pu[s], pv = ix.pv[s];
-                if (pu == POS_OVF) {
-                    ovf[pv] = TOMB_KEY;
-                } else {
-                    g.col[pu] = -1;
-                    g.col[pv] = -1;
+        if (i < len) {
+            int u = batch[2 * i], v = batch[2 * i + 1];
+            bool won = false;
+            if (u != v) {
+                u64 key = ekey((uint32_t)u, (uint32_t)v);
+                long long s = index_find(ix, key);
+                if (s >= 0) won = atomicCAS(&ix.key[s], key, TOMB_KEY) == key;
+                if (won) {
+                    uint32_t pu = ix.pu[s], pv = ix.pv[s];
+                    if (pu == POS_OVF) {
+                        ovf[pv] = TOMB_KEY;
+                    } else {
+                        g.col[pu] = -1;
+                        g.col[pv] = -1;
+                    }
+                    if (parent[u] == v) c = u;
+                    else if (parent[v] == u) c = v;
+                    if (c >= 0) {
+                        parent[c] = c;
+                        cut_ep[c] = ep;
+                        w[c] = 0;   // c roots a new piece: its weight slot
+                    }
                 }
-                if (parent[u] == v) c = u;
-                else if (parent[v] == u) c = v;
-                if (c >= 0) {
-                    parent[c] = c;
-                    cut_ep[c] = ep;
-                    w[c] = 0;   // c roots a new piece: its weight slot
-                }
+                wins += won;
+                drops += !won;
+            } else {
+                ++loops;
             }
         }
         {
             // stamp the cut trees' old roots; lanes cutting the same tree
             // write once (most cuts can fall in one giant tree)
             int r = c >= 0 ? rep[c] : -1;
-            unsigned m = __ballot_sync(__activemask(), c >= 0);
+            unsigned m = __ballot_sync(0xffffffffu, c >= 0);
             if (c >= 0) {
                 unsigned grp = __match_any_sync(m, r);
                 if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) aff_ep[r] = ep;
             }
         }
-        agg_count(&ctl->self_loops, u == v);
-        agg_count(&ctl->dropped, u != v && !won);
-        agg_count(&ctl->htomb, won);
-        agg_count(&ctl->edges, won, -1);
-        agg_append(&ctl->nb, won);
-        long long p = agg_append(&ctl->ncut, c >= 0);
+        long long p = block_append(&ctl->ncut, c >= 0);
         if (c >= 0) cutlist[p] = c;
     }
+    block_add(&ctl->self_loops, loops);
+    block_add(&ctl->dropped, drops);
+    block_add(&ctl->htomb, wins);
+    block_add(&ctl->edges, -wins);
+    block_add((long long *)&ctl->nb, wins);
 }
 
 // Delete, cross-edge scan (key edges M = E(G) - E(F) - B, Algorithm 1,
-// restricted).  The rows of the listed vertices D (every vertex outside the
-// heaviest piece of its cut tree) are flattened by the prefix sum roff, and
+// restricted).  The rows of the listed vertices (every vertex outside the
+// piece left out of its cut tree) are flattened by the prefix sum roff, and
 // each warp takes 32 consecutive entries, whatever rows they fall in (load
 // balanced: a hub row is spread over many warps, short rows share a warp).
-// Lane e finds its row among the 32 rows starting at the row of the warp's
-// first entry (found by binary search).  A live neighbour x of u in another
+// The warp loads the list entries of the 32 rows starting at the row of its
+// first entry (one coalesced load per field), and lane e takes its row's
+// fields from the lane that loaded them, so an entry costs one column load
+// and one rep gather after the window.  A live neighbour x of u in another
 // piece gives the cross edge {u, x}; every cross edge has a listed endpoint
 // and, when both are listed, the smaller id emits it.  Parallel edges
 // between two pieces are reduced to the one with the minimum key, which is
 // the only one that can be in the minimum spanning forest: lanes holding the
 // same piece pair take the minimum first, then one lane updates the pair
 // table.  A pair that finds no table slot is emitted as a plain candidate.
-__global__ void k_scan_lb(const int *D, const long long *roff, Ctl *ctl, Csr g, const int *rep, const int *rold,
-                          const u64 *heavy, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap) {
+__global__ void k_scan_lb(RowList rl, Ctl *ctl, Csr g, const int *rep, PairTable pt, u64 *ck, int *ca, int *cb,
+                          u64 cand_cap) {
     if (*(volatile int *)&ctl->skip) return;
     const long long nd = (long long)ctl->ndet;
     if (nd == 0) return;
+    const long long *roff = rl.roff;
     const long long E = roff[nd];
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -360,39 +389,43 @@ __global__ void k_scan_lb(const int *D, const long long *roff, Ctl *ctl, Csr g, 
     r0 = __shfl_sync(0xffffffffu, r0, 0);
     for (long long t0 = e_lo; t0 < e_hi; t0 += 32) {
         const long long e = t0 + lane;
-        // rows r0 .. r0+31 start at wv; the rows after r0 that start inside
-        // this tile set a bit at their start position, and the row of
-        // position q is r0 plus the number of such starts at positions <= q
-        const long long wv = r0 + lane < nd ? roff[r0 + lane] : LLONG_MAX;
+        // window: rows r0 .. r0+31 (start wv, vertex, CSR start, pieces)
+        const long long wr = r0 + lane;
+        const bool wok = wr < nd;
+        const long long wv = wok ? roff[wr] : LLONG_MAX;
+        const int wu = wok ? rl.D[wr] : 0;
+        const long long wb = wok ? rl.base[wr] : 0;
+        const int2 wm = wok ? rl.meta[wr] : make_int2(0, 0);
+        // the rows after r0 that start inside this tile set a bit at their
+        // start position; the row of position q is r0 plus the number of
+        // such starts at positions <= q
         const long long pos = wv - t0;
         const unsigned bit = (lane > 0 && pos >= 0 && pos < 32) ? (1u << pos) : 0u;
         const unsigned starts = __reduce_or_sync(0xffffffffu, bit);
         const int c = __popc(starts & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u)));
-        const long long r = r0 + c;
-        const long long rstart = __shfl_sync(0xffffffffu, wv, c);   // all lanes take part
-        bool emit = false;
-        int u = 0, x = -1, ru = 0, rx = 0;
-        if (e < e_hi) {
-            u = D[r];
-            long long j = e - rstart;
-            x = __ldcs(&g.col[g.off[u] + j]);
-            if (x >= 0) {
-                ru = rep[u];
-                rx = rep[x];
-                if (rx != ru) {
-                    int hp = (int)(unsigned)heavy[rold[u]];
-                    emit = rx == hp || u < x;
-                }
-            }
-        }
+        // all lanes take part in the shuffles
+        const long long rstart = __shfl_sync(0xffffffffu, wv, c);
+        const int u = __shfl_sync(0xffffffffu, wu, c);
+        const long long rb = __shfl_sync(0xffffffffu, wb, c);
+        const int ru = __shfl_sync(0xffffffffu, wm.x, c);
+        const int hp = __shfl_sync(0xffffffffu, wm.y, c);
         // the next tile starts at t0 + 32: in the row of this tile's last
         // entry or the one after it (rows are never empty); the window of
         // the next tile must start exactly at that row
         {
-            long long r31 = __shfl_sync(0xffffffffu, r, 31);
-            long long nx = r31;
-            if (lane == 31 && r31 + 1 < nd && roff[r31 + 1] <= t0 + 32) nx = r31 + 1;
-            r0 = __shfl_sync(0xffffffffu, nx, 31);
+            const int c31 = __shfl_sync(0xffffffffu, c, 31);
+            long long nstart = __shfl_sync(0xffffffffu, wv, c31 < 31 ? c31 + 1 : 31);
+            if (c31 == 31) nstart = r0 + 32 < nd ? roff[r0 + 32] : LLONG_MAX;
+            r0 += c31 + (nstart <= t0 + 32 ? 1 : 0);
+        }
+        bool emit = false;
+        int x = -1, rx = 0;
+        if (e < e_hi) {
+            x = __ldcs(&g.col[rb + (e - rstart)]);
+            if (x >= 0) {
+                rx = rep[x];
+                if (rx != ru) emit = rx == hp || u < x;
+            }
         }
         unsigned m = __ballot_sync(0xffffffffu, emit);
         bool raw = false;
@@ -447,21 +480,40 @@ __global__ void k_scan_ovf(const u64 *ovf, Ctl *ctl, const int *rep, PairTable p
 // pair, its minimum key) and free the slots for the next batch.
 __global__ void k_pairs_compact(Ctl *ctl, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap) {
     if (*(volatile int *)&ctl->skip) return;
-    GS_LOOP(i, pt.mask + 1) {
-        u64 pair = pt.pk[i];
-        bool on = pair != EMPTY_KEY;
-        u64 k = 0;
-        if (on) {
-            k = pt.mk[i];
-            pt.pk[i] = EMPTY_KEY;
-            pt.mk[i] = EMPTY_KEY;
+    // four slots per thread and iteration, one counter reservation per
+    // block (the table has far more slots than warps have lanes, and most
+    // warps hold an occupied slot: a per-warp append would queue on the
+    // counter)
+    const long long T = (long long)pt.mask + 1;
+    const long long S = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < T; base += 4 * S) {
+        u64 pair[4], k[4];
+        bool on[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            long long i = base + q * S + threadIdx.x;
+            pair[q] = i < T ? pt.pk[i] : EMPTY_KEY;
+            on[q] = pair[q] != EMPTY_KEY;
         }
-        long long p = agg_append(&ctl->ncand, on);
-        if (on) {
-            if ((u64)p < cand_cap) {
-                ck[p] = k;
-                ca[p] = (int)(pair >> 32);
-                cb[p] = (int)(pair & 0xFFFFFFFFu);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            k[q] = 0;
+            if (on[q]) {
+                long long i = base + q * S + threadIdx.x;
+                k[q] = pt.mk[i];
+                pt.pk[i] = EMPTY_KEY;
+                pt.mk[i] = EMPTY_KEY;
+            }
+        }
+        long long p[4];
+        block_reserve4(&ctl->ncand, on, p);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!on[q]) continue;
+            if ((u64)p[q] < cand_cap) {
+                ck[p[q]] = k[q];
+                ca[p[q]] = (int)(pair[q] >> 32);
+                cb[p[q]] = (int)(pair[q] & 0xFFFFFFFFu);
             } else {
                 atomicOr(&ctl->err, ERR_CAPACITY);
             }
@@ -585,10 +637,9 @@ cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u
     k_del_claim<<<gsz(len), BLK, 0, s>>>(batch, len, ix, g, ovf, parent, rep, ctl, aff_ep, cut_ep, cutlist, w);
     return cudaGetLastError();
 }
-cudaError_t launch_scan_rows(const Dev &d, const int *D, const long long *roff, Ctl *ctl, Csr g, const int *rep,
-                             const int *rold, const u64 *heavy, PairTable pt, u64 *ck, int *ca, int *cb,
-                             u64 cand_cap, cudaStream_t s) {
-    k_scan_lb<<<d.grid, BLK, 0, s>>>(D, roff, ctl, g, rep, rold, heavy, pt, ck, ca, cb, cand_cap);
+cudaError_t launch_scan_rows(const Dev &d, RowList rl, Ctl *ctl, Csr g, const int *rep, PairTable pt, u64 *ck,
+                             int *ca, int *cb, u64 cand_cap, cudaStream_t s) {
+    k_scan_lb<<<d.grid, BLK, 0, s>>>(rl, ctl, g, rep, pt, ck, ca, cb, cand_cap);
     return cudaGetLastError();
 }
 cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, PairTable pt, u64 *ck, int *ca,
@@ -598,7 +649,8 @@ cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *r
 }
 cudaError_t launch_pairs_compact(const Dev &d, Ctl *ctl, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap,
                                  cudaStream_t s) {
-    k_pairs_compact<<<gsz((long long)pt.mask + 1), BLK, 0, s>>>(ctl, pt, ck, ca, cb, cand_cap);
+    k_pairs_compact<<<grid_for(((long long)pt.mask + 4) / 4, BLK, (unsigned)d.nsm * 8u), BLK, 0, s>>>(ctl, pt, ck, ca,
+                                                                                                   cb, cand_cap);
     return cudaGetLastError();
 }
 cudaError_t launch_extract(const Dev &d, int n, Csr g, const u64 *ovf, u64 novf_max, Ctl *ctl, int *out,

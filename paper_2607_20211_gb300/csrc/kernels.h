@@ -35,14 +35,23 @@ cudaError_t launch_ins_place(const Dev &d, const u64 *nkey, const u64 *nslot, Ct
 cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u64 *ovf, int *parent,
                              const int *rep, Ctl *ctl, unsigned *aff_ep, unsigned *cut_ep, int *cutlist,
                              unsigned *w, cudaStream_t s);
+// The rows a delete batch scans for cross edges, one entry per listed
+// vertex u: u itself, the exclusive prefix sum of the row lengths (roff[nd]
+// = total), the row's start in the CSR, and (rep[u], piece left out of the
+// scan in u's tree).
+struct RowList {
+    int *D;
+    long long *roff;
+    long long *base;
+    int2 *meta;
+};
 struct PairTable {
     u64 *pk;   // piece pair key, EMPTY_KEY when free
     u64 *mk;   // minimum edge key of the pair
     u64 mask;
 };
-cudaError_t launch_scan_rows(const Dev &d, const int *D, const long long *roff, Ctl *ctl, Csr g, const int *rep,
-                             const int *rold, const u64 *heavy, PairTable pt, u64 *ck, int *ca, int *cb,
-                             u64 cand_cap, cudaStream_t s);
+cudaError_t launch_scan_rows(const Dev &d, RowList rl, Ctl *ctl, Csr g, const int *rep, PairTable pt, u64 *ck,
+                             int *ca, int *cb, u64 cand_cap, cudaStream_t s);
 cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, PairTable pt, u64 *ck, int *ca,
                             int *cb, u64 cand_cap, cudaStream_t s);
 cudaError_t launch_pairs_compact(const Dev &d, Ctl *ctl, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap,
@@ -58,9 +67,8 @@ cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsign
                                int *J0, int *A, int *rold, unsigned *w, u64 *heavy, Ctl *ctl, cudaStream_t s);
 cudaError_t launch_copy_parent(int n, const int *parent, int *J0, cudaStream_t s);
 cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1,
-                        int *rep, int *D, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g,
-                        long long *roff, long long *bsum, int sync_rounds, int *X, int *Y, const int *cuts,
-                        cudaStream_t s);
+                        int *rep, RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g,
+                        long long *bsum, int sync_rounds, int *X, int *Y, const int *cuts, cudaStream_t s);
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
                            int *comp, u64 *best0, u64 *best1, u64 *er, long long er_cap, cudaStream_t s);
 struct OrientArgs {
@@ -80,8 +88,10 @@ struct OrientArgs {
     int *eroot;          // per edge: hook-forest root of its super-tree
 };
 cudaError_t launch_orient(const Dev &d, Ctl *ctl, OrientArgs a, cudaStream_t s);
+cudaError_t launch_walk(const Dev &d, Ctl *ctl, const int *chx, const int *chy, const int *rep, int *parent,
+                        unsigned *long_ep, cudaStream_t s);
 cudaError_t launch_active(const Dev &d, const int *L, int use_list, long long cnt_static, Ctl *ctl, int *rep,
-                          const int *parent, const unsigned *att_ep, const int *att_x, const unsigned *rep_ep,
+                          const int *parent, const unsigned *sel_ep, const int *att_x, const unsigned *rep_ep,
                           const int *newrep, int *act, int *pold, int *J0, unsigned char *mark, int *aidx,
                           int *aroot, cudaStream_t s);
 cudaError_t launch_mark(const Dev &d, Ctl *ctl, const int *act, int *J0, int *J1, unsigned char *mark,

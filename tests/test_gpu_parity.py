@@ -124,6 +124,38 @@ def test_long_path_reversal():
     f.close()
 
 
+def test_walk_length_boundary():
+    """Re-rooted paths of 1 .. 130 edges in one batch, around the 64-edge
+    limit of the walking reversal (longer paths go through the marks):
+    paths hang below their top vertex, vertex 0 is a lone root with the
+    smallest id, and one insert joins each path's deepest vertex to 0, so
+    every path is re-rooted at its deep end."""
+    lengths = [1, 2, 31, 63, 64, 65, 66, 100, 130]
+    n = 1 + sum(L + 1 for L in lengths)
+    edges, parent = [], [0]
+    leaves, tops, v = [], [], 1
+    for L in lengths:
+        top = v
+        parent.append(top)
+        for k in range(1, L + 1):
+            edges.append((v + k - 1, v + k))
+            parent.append(v + k - 1)
+        tops.append(top)
+        leaves.append(v + L)
+        v += L + 1
+    g = _tiny(n, edges, parent)
+    f = make_forest(g)
+    b = np.array([[leaf, 0] for leaf in leaves], np.int32)
+    keys, par, st = check_batch(f, n, g.keys, g.parent, I, b)
+    assert st["reversed"] == sum(lengths)
+    # cut every path in its middle and join the halves back through 0
+    b = np.array([[tops[i] + L // 2, tops[i] + L // 2 + 1] for i, L in enumerate(lengths)], np.int32)
+    keys, par, st = check_batch(f, n, keys, par, D, b)
+    b = np.array([[t, 0] for t in tops], np.int32)
+    check_batch(f, n, keys, par, I, b)
+    f.close()
+
+
 def test_invalid_id_skips_batch():
     g = workloads.er_graph(1000, 1500, seed=7)
     f = make_forest(g)
