@@ -53,7 +53,7 @@ struct drsf_ctx {
     int *att_x = nullptr, *newrep = nullptr, *A = nullptr, *act = nullptr, *pold = nullptr, *D = nullptr;
     int *chx = nullptr, *chy = nullptr;
     unsigned *aff_ep = nullptr, *cut_ep = nullptr, *pstamp = nullptr, *att_ep = nullptr, *rep_ep = nullptr;
-    unsigned *long_ep = nullptr;
+    unsigned *long_ep = nullptr, *hstamp = nullptr;
     u64 *best0 = nullptr, *best1 = nullptr, *er = nullptr, *heavy = nullptr;
     int *rold = nullptr, *cdeg = nullptr, *xlist = nullptr, *aidx = nullptr, *aroot = nullptr;
     int *oep = nullptr, *oeid = nullptr, *oeroot = nullptr;
@@ -108,7 +108,7 @@ enum {
     PH_ORIENT,        // Euler-tour orientation
     PH_ACTIVE,        // path-reversal set-up + representative refresh
     PH_MARK,          // pointer-doubling marks
-    PH_REVERSE        // reversal scatter + attach
+    PH_REVERSE        // path walks, reversal scatter + attach
 };
 static const char *kPhaseNames[DRSF_NUM_PHASES] = {
     "begin", "ins_claim", "ins_place", "del_claim", "affected", "jump", "scan", "hook", "orient", "active",
@@ -424,6 +424,7 @@ static drsf_status alloc_work(drsf_ctx *h, cudaStream_t s) {
     CKA(halloc(h, &h->pstamp, n, s));
     CKA(halloc(h, &h->att_ep, n, s));
     CKA(halloc(h, &h->long_ep, n, s));
+    CKA(halloc(h, &h->hstamp, n, s));
     CKA(halloc(h, &h->rep_ep, n, s));
     CKA(halloc(h, &h->best0, n, s));
     CKA(halloc(h, &h->best1, n, s));
@@ -454,7 +455,7 @@ static drsf_status alloc_work(drsf_ctx *h, cudaStream_t s) {
     CKA(halloc(h, &h->nx1, 2 * n + 2, s));
     CKA(halloc(h, &h->bsum, 8192, s));
     CKA(halloc(h, &h->ctl, 1, s));
-    unsigned *eps[] = {h->aff_ep, h->cut_ep, h->pstamp, h->att_ep, h->rep_ep, h->long_ep};
+    unsigned *eps[] = {h->aff_ep, h->cut_ep, h->pstamp, h->att_ep, h->rep_ep, h->long_ep, h->hstamp};
     for (unsigned *e : eps) CK(cudaMemsetAsync(e, 0, n * sizeof(unsigned), s));
     CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
     return DRSF_OK;
@@ -632,7 +633,7 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
     }
     prof_begin(h, PH_HOOK, s);
     CK(launch_boruvka(h->dev, ctl, h->ck[0], h->ca[0], h->cb[0], h->ck[1], h->ca[1], h->cb[1], h->comp, h->best0,
-                      h->best1, h->er, h->n, s));
+                      h->best1, h->er, h->n, h->hstamp, s));
     prof_end(h, PH_HOOK, 1, s);
     OrientArgs oa{};
     oa.er = h->er;
@@ -711,7 +712,7 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
     prof_end(h, PH_MARK, 1, s);
     prof_begin(h, PH_REVERSE, s);
     CK(launch_reverse(h->dev, ctl, h->act, h->pold, h->mark, h->chx, h->chy, h->parent, s));
-    prof_end(h, PH_REVERSE, 2, s);
+    prof_end(h, PH_REVERSE, 1, s);
     return DRSF_OK;
 }
 

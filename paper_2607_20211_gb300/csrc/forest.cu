@@ -23,8 +23,6 @@
 #define ORIENT_THREADS 1024
 // independent items per thread and iteration in the pointer-doubling rounds
 #define JU 4
-// the same for the final pass of the jump (more state per item)
-#define JF 2
 // consecutive items per thread in the list-building vertex passes
 #define IPT 4
 // longest path reversed by one walking thread (longer ones: doubling marks)
@@ -160,6 +158,9 @@ __device__ __forceinline__ void piece_count(int *s_wk, unsigned *s_wc, unsigned 
 // detaches most of a tree): then the heaviest piece.  The listed rows get an
 // exclusive prefix sum of their lengths in roff (roff[ndet] = total), their
 // CSR start and their (piece, piece left out) for the load-balanced scan.
+// In delete mode a vertex is settled in the round its pointer reaches a
+// root (no extra pass over the list): its representative, its piece's
+// weight and, outside the root piece, its entry in the provisional row list.
 // (6 blocks of BLK threads per SM: the rounds are latency-bound)
 __global__ void __launch_bounds__(BLK, 6)
     k_jump(const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1, int *rep, RowList rl, int mode,
@@ -181,6 +182,15 @@ __global__ void __launch_bounds__(BLK, 6)
         // either buffer see the root.
         int *Jc = J, *Jn = J1;
         int r = 0;
+        // piece-count table of the block (open addressing; counts go to
+        // global memory once per piece and block, or directly when the
+        // table has no slot)
+        __shared__ int s_wk[WT_SLOTS];
+        __shared__ unsigned s_wc[WT_SLOTS];
+        for (int t = threadIdx.x; t < WT_SLOTS; t += blockDim.x) {
+            s_wk[t] = -1;
+            s_wc[t] = 0;
+        }
         if (gtid() == 0) {
             ctl->cnt[0] = (u64)cnt;
             ctl->cnt[1] = 0;
@@ -203,7 +213,7 @@ __global__ void __launch_bounds__(BLK, 6)
             // are issued together (more loads in flight per thread)
             const long long S = gstride();
             for (long long base = (long long)blockIdx.x * blockDim.x; base < c; base += S * JU) {
-                int v[JU], w0[JU], w2[JU];
+                int v[JU], w0[JU], w2[JU], ro[JU];
                 bool ok[JU], open[JU];
 #pragma unroll
                 for (int k = 0; k < JU; ++k) {
@@ -212,10 +222,12 @@ __global__ void __launch_bounds__(BLK, 6)
                     v[k] = ok[k] ? (in ? in[i] : (int)i) : 0;
                 }
 #pragma unroll
-                for (int k = 0; k < JU; ++k) w0[k] = ok[k] ? LD(Jc[v[k]]) : -1;
+                for (int k = 0; k < JU; ++k) {
+                    w0[k] = ok[k] ? LD(Jc[v[k]]) : -1;
+                    ro[k] = (mode && ok[k]) ? rold[v[k]] : 0;
+                }
 #pragma unroll
                 for (int k = 0; k < JU; ++k) w2[k] = (ok[k] && w0[k] >= 0) ? LD(Jc[w0[k]]) : 0;
-                int nopen = 0;
 #pragma unroll
                 for (int k = 0; k < JU; ++k) {
                     open[k] = false;
@@ -227,17 +239,52 @@ __global__ void __launch_bounds__(BLK, 6)
                     else {
                         nv = w2[k];
                         open[k] = true;
-                        ++nopen;
                     }
                     Jn[v[k]] = nv;
                     if (!open[k]) Jc[v[k]] = nv;
+                    w0[k] = ~nv;   // the root once converged
                 }
-                (void)nopen;
                 long long q[JU];
                 block_reserve4(&ctl->cnt[(r + 1) % 3], open, q);
 #pragma unroll
                 for (int k = 0; k < JU; ++k)
                     if (open[k]) out[q[k]] = v[k];
+                if (!mode) continue;
+                // delete: a vertex is settled in the round it converges:
+                // its representative (written only when it left its tree's
+                // root piece), its piece's weight, and the provisional list
+                // of rows to scan (vertices outside the root piece)
+                bool scan[JU];
+#pragma unroll
+                for (int k = 0; k < JU; ++k) {
+                    w2[k] = 0;   // the row length of a listed vertex
+                    if (ok[k] && !open[k] && w0[k] != ro[k]) {
+                        rep[v[k]] = w0[k];
+                        int cap = (int)(g.off[v[k] + 1] - g.off[v[k]]);
+                        int used = g.used[v[k]];
+                        w2[k] = used < cap ? used : cap;
+                    }
+                    scan[k] = w2[k] > 0;
+                }
+#pragma unroll
+                for (int k = 0; k < JU; ++k) {
+                    bool settled = ok[k] && !open[k];
+                    unsigned vm = __ballot_sync(0xffffffffu, settled);
+                    if (settled) {
+                        unsigned grp = __match_any_sync(vm, w0[k]);
+                        if ((int)(threadIdx.x & 31) == __ffs(grp) - 1)
+                            piece_count(s_wk, s_wc, w, w0[k], (unsigned)__popc(grp));
+                    }
+                }
+                block_reserve4(&ctl->ndet, scan, q);
+#pragma unroll
+                for (int k = 0; k < JU; ++k)
+                    if (scan[k]) {
+                        D[q[k]] = v[k];
+                        roff[q[k]] = w2[k];
+                        rl.base[q[k]] = g.off[v[k]];
+                        rl.meta[q[k]] = make_int2(w0[k], ro[k]);
+                    }
             }
             if (!grid_barrier(ctl, &ctl->bar[0])) return;
             int *t = Jc; Jc = Jn; Jn = t;
@@ -250,70 +297,7 @@ __global__ void __launch_bounds__(BLK, 6)
             }
             return;
         }
-        // final pass: representatives, piece weights (vertex counts; the
-        // weight slots of piece roots were zeroed at the cut) and a
-        // provisional list of rows to scan: every vertex outside its tree's
-        // root piece (only those read their row length).  JU vertices per
-        // thread and iteration.  Piece counts go to a small open-addressing
-        // table in shared memory (one global atomic per piece and block at
-        // the end; a large piece spans many blocks), or straight to global
-        // memory when the table has no slot.
-        __shared__ int s_wk[WT_SLOTS];
-        __shared__ unsigned s_wc[WT_SLOTS];
-        for (int t = threadIdx.x; t < WT_SLOTS; t += blockDim.x) {
-            s_wk[t] = -1;
-            s_wc[t] = 0;
-        }
-        __syncthreads();
-        const long long S = gstride();
-        for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += S * JF) {
-            int v[JF], p[JF], ro[JF], len[JF];
-            bool ok[JF], scan[JF];
-#pragma unroll
-            for (int k = 0; k < JF; ++k) {
-                long long i = base + k * S + threadIdx.x;
-                ok[k] = i < cnt;
-                v[k] = ok[k] ? A[i] : 0;
-            }
-#pragma unroll
-            for (int k = 0; k < JF; ++k) {
-                p[k] = ok[k] ? ~LD(Jc[v[k]]) : 0;
-                ro[k] = ok[k] ? rold[v[k]] : 0;
-            }
-#pragma unroll
-            for (int k = 0; k < JF; ++k) {
-                scan[k] = false;
-                len[k] = 0;
-                if (!ok[k]) continue;
-                rep[v[k]] = p[k];
-                if (p[k] != ro[k]) {
-                    int cap = (int)(g.off[v[k] + 1] - g.off[v[k]]);
-                    int used = g.used[v[k]];
-                    len[k] = used < cap ? used : cap;
-                    scan[k] = len[k] > 0;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < JF; ++k) {
-                unsigned vm = __ballot_sync(0xffffffffu, ok[k]);
-                if (ok[k]) {
-                    unsigned grp = __match_any_sync(vm, p[k]);
-                    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
-                        piece_count(s_wk, s_wc, w, p[k], (unsigned)__popc(grp));
-                    }
-                }
-            }
-            long long q[JF];
-            block_reserve2(&ctl->ndet, scan, q);
-#pragma unroll
-            for (int k = 0; k < JF; ++k)
-                if (scan[k]) {
-                    D[q[k]] = v[k];
-                    roff[q[k]] = len[k];
-                    rl.base[q[k]] = g.off[v[k]];
-                    rl.meta[q[k]] = make_int2(p[k], ro[k]);
-                }
-        }
+        // piece weights counted while settling
         __syncthreads();
         for (int t = threadIdx.x; t < WT_SLOTS; t += blockDim.x)
             if (s_wk[t] != -1) atomicAdd(&w[s_wk[t]], s_wc[t]);
@@ -446,24 +430,100 @@ __global__ void __launch_bounds__(BLK, 6)
 // component are dropped, the rest are compacted for the next round.  With
 // distinct keys this is Boruvka's algorithm: E_r is the unique minimum
 // spanning forest of the piece multigraph, |E_r| = k - l.
-__global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1, int *comp,
-                          u64 *best0, u64 *best1, u64 *er, long long er_cap) {
-    if (*(volatile int *)&ctl->skip) return;
-    long long c0 = (long long)ctl->ncand;
-    for (long long i = gtid(); i < c0; i += gstride()) {
-        int a = ca0[i], b = cb0[i];
-        // one lane per distinct piece writes (a piece such as the giant one
-        // can be an endpoint of most candidates)
-        unsigned act = __activemask();
-        unsigned ga = __match_any_sync(act, a), gb = __match_any_sync(act, b);
-        int lane = threadIdx.x & 31;
-        if (lane == __ffs(ga) - 1) {
-            comp[a] = a;
-            best0[a] = best1[a] = EMPTY_KEY;
+// Per-block table of hot indices for 64-bit minimum updates: lanes of a
+// warp with the same index combine first; an index held by two or more
+// lanes of a warp (one piece, such as the giant one, can be an endpoint of
+// most candidates) is combined in shared memory and sent to global memory
+// once per block by hm_flush; a lone index goes straight to global memory.
+#define HM_SLOTS 16
+#define HM_PROBES 4
+struct HotMin {
+    int k[HM_SLOTS];
+    u64 v[HM_SLOTS];
+    int rst[HM_SLOTS];
+};
+__device__ __forceinline__ void hm_init(HotMin &t) {
+    for (int i = threadIdx.x; i < HM_SLOTS; i += blockDim.x) {
+        t.k[i] = -1;
+        t.v[i] = EMPTY_KEY;
+        t.rst[i] = 0;
+    }
+    __syncthreads();
+}
+// slot of idx in the table (inserted when ins and absent), or -1
+__device__ __forceinline__ int hm_slot(HotMin &t, int idx, bool ins) {
+    unsigned h = ((unsigned)idx * 0x9E3779B1u) >> 28;
+    for (int p = 0; p < HM_PROBES; ++p) {
+        int key = *(volatile int *)&t.k[h];
+        if (key == -1 && ins) key = atomicCAS(&t.k[h], -1, idx);
+        if (key == idx || (key == -1 && ins)) return (int)h;
+        if (key == -1) return -1;
+        h = (h + 1) & (HM_SLOTS - 1);
+    }
+    return -1;
+}
+__device__ __forceinline__ void hm_min(HotMin &t, u64 *arr, int idx, u64 k, bool pred) {
+    unsigned m = __ballot_sync(__activemask(), pred);
+    if (!pred) return;
+    unsigned grp = __match_any_sync(m, idx);
+    u64 kmin = group_min_u64(grp, k);
+    if ((int)(threadIdx.x & 31) != __ffs(grp) - 1) return;
+    int sl = __popc(grp) > 1 ? hm_slot(t, idx, true) : -1;
+    if (sl >= 0) atomicMin(&t.v[sl], kmin);
+    else atomicMin(&arr[idx], kmin);
+}
+// bestn[idx] = EMPTY_KEY, once per block for the table's indices
+__device__ __forceinline__ void hm_reset(HotMin &t, u64 *arr, int idx, bool pred) {
+    unsigned m = __ballot_sync(__activemask(), pred);
+    if (!pred) return;
+    unsigned grp = __match_any_sync(m, idx);
+    if ((int)(threadIdx.x & 31) != __ffs(grp) - 1) return;
+    int sl = __popc(grp) > 1 ? hm_slot(t, idx, true) : -1;
+    if (sl >= 0) t.rst[sl] = 1;
+    else arr[idx] = EMPTY_KEY;
+}
+// sends the table's minima to arr (min) and its resets to rst_arr, then
+// clears it; every thread of the block calls it
+__device__ __forceinline__ void hm_flush(HotMin &t, u64 *arr, u64 *rst_arr) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < HM_SLOTS; i += blockDim.x) {
+        if (t.k[i] != -1) {
+            if (t.v[i] != EMPTY_KEY) atomicMin(&arr[t.k[i]], t.v[i]);
+            if (t.rst[i]) rst_arr[t.k[i]] = EMPTY_KEY;
         }
-        if (lane == __ffs(gb) - 1) {
-            comp[b] = b;
-            best0[b] = best1[b] = EMPTY_KEY;
+        t.k[i] = -1;
+        t.v[i] = EMPTY_KEY;
+        t.rst[i] = 0;
+    }
+    __syncthreads();
+}
+
+// Replacement edges by hook-and-compress over the trees of F^ (pieces).
+// Each round: every component takes the minimum key among its incident
+// candidates (64-bit atomicMin); a component whose minimum edge leads to
+// another component hooks onto it (a mutual choice hooks the larger id under
+// the smaller); each hooking edge joins E_r.  Candidates inside one
+// component are dropped, the rest are compacted for the next round.  With
+// distinct keys this is Boruvka's algorithm: E_r is the unique minimum
+// spanning forest of the piece multigraph, |E_r| = k - l.
+__global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1, int *comp,
+                          u64 *best0, u64 *best1, u64 *er, long long er_cap, unsigned *hstamp) {
+    if (*(volatile int *)&ctl->skip) return;
+    __shared__ HotMin hm;
+    const unsigned ep = ctl->epoch;
+    long long c0 = (long long)ctl->ncand;
+    // initialise each candidate endpoint once (the first lane to stamp it)
+    for (long long i = gtid(); i < c0; i += gstride()) {
+        int e2[2] = {ca0[i], cb0[i]};
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int a = e2[s];
+            unsigned grp = __match_any_sync(__activemask(), a);
+            if ((int)(threadIdx.x & 31) == __ffs(grp) - 1 && __ldcg(&hstamp[a]) != ep &&
+                atomicExch(&hstamp[a], ep) != ep) {
+                comp[a] = a;
+                best0[a] = best1[a] = EMPTY_KEY;
+            }
         }
     }
     if (gtid() == 0) {
@@ -471,6 +531,7 @@ __global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int 
         ctl->cnt[1] = ctl->cnt[2] = 0;
         ctl->flag[0] = ctl->flag[1] = ctl->flag[2] = 0;
     }
+    hm_init(hm);
     if (!grid_barrier(ctl, &ctl->bar[1])) return;
     int r = 0;
     for (;; ++r) {
@@ -489,21 +550,33 @@ __global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int 
         }
         // phase A: roots of both ends, per-component minimum key
         for (long long i = gtid(); i < c; i += gstride()) {
-            int a = find_root(comp, LD(ca[i]), ctl), b = find_root(comp, LD(cb[i]), ctl);
-            ca[i] = a;
-            cb[i] = b;
-            u64 k = LD(ck[i]);
-            warp_atomic_min_u64(best, a, k, a != b);
-            warp_atomic_min_u64(best, b, k, a != b);
-        }
-        if (!grid_barrier(ctl, &ctl->bar[1])) return;
-        // phase B: hook along minimum edges, keep the rest
-        bool hooked = false;
-        for (long long i = gtid(); i < c; i += gstride()) {
             int a = LD(ca[i]), b = LD(cb[i]);
-            bool alive = a != b;
-            bool hook = false, keep = false;
+            if (r > 0) {   // every endpoint is its own root in round 0
+                a = find_root(comp, a, ctl);
+                b = find_root(comp, b, ctl);
+                ca[i] = a;
+                cb[i] = b;
+            }
             u64 k = LD(ck[i]);
+            hm_min(hm, best, a, k, a != b);
+            hm_min(hm, best, b, k, a != b);
+        }
+        hm_flush(hm, best, bestn);
+        if (!grid_barrier(ctl, &ctl->bar[1])) return;
+        // phase B: hook along minimum edges, keep the rest (block-uniform
+        // loop: list appends are reserved once per block)
+        bool hooked = false;
+        for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < c; b0 += gstride()) {
+            const long long i = b0 + threadIdx.x;
+            int a = 0, b = 0;
+            bool alive = false, hook = false, keep = false;
+            u64 k = 0;
+            if (i < c) {
+                a = LD(ca[i]);
+                b = LD(cb[i]);
+                alive = a != b;
+                k = LD(ck[i]);
+            }
             if (alive) {
                 bool ba = __ldcg(&best[a]) == k, bb = __ldcg(&best[b]) == k;
                 if (ba && bb) comp[a > b ? a : b] = a > b ? b : a;
@@ -511,22 +584,23 @@ __global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int 
                 else if (bb) comp[b] = a;
                 hook = ba || bb;
                 keep = !hook;
-                bestn[a] = EMPTY_KEY;
-                bestn[b] = EMPTY_KEY;
             }
+            hm_reset(hm, bestn, a, alive);
+            hm_reset(hm, bestn, b, alive);
             hooked |= hook;
-            long long pe = agg_append(&ctl->ner, hook);
+            long long pe = block_append(&ctl->ner, hook);
             if (hook) {
                 if (pe < er_cap) er[pe] = k;
                 else atomicOr(&ctl->err, ERR_CAPACITY);
             }
-            long long pk = agg_append(&ctl->cnt[(r + 1) % 3], keep);
+            long long pk = block_append(&ctl->cnt[(r + 1) % 3], keep);
             if (keep) {
                 ckn[pk] = k;
                 can[pk] = a;
                 cbn[pk] = b;
             }
         }
+        hm_flush(hm, best, bestn);
         if (__syncthreads_or(hooked) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
         if (!grid_barrier(ctl, &ctl->bar[1])) return;
         if (!*(volatile int *)&ctl->flag[r % 3]) break;
@@ -581,6 +655,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS) k_orient(Ctl *ctl, OrientArgs 
     // (ep), later phases its dense id (eid) and each edge's super-tree root
     // (eroot), so no phase re-walks rep / pidx / the hook forest.
     // phase 1: dense ids for the pieces touched by E_r
+    if (gtid() == 0) ctl->ncore = 0;
     for (long long j = gtid(); j < 2 * ner; j += gstride()) {
         u64 k = a.er[j >> 1];
         int p = a.rep[(j & 1) ? khi(k) : klo(k)];
@@ -638,44 +713,15 @@ __global__ void __launch_bounds__(ORIENT_THREADS) k_orient(Ctl *ctl, OrientArgs 
         }
     }
     if (!grid_barrier(ctl, bar)) return;
-    // phase 3: exclusive scan of core degrees -> adjacency offsets
+    // phase 3: adjacency ranges of the core pieces, reserved per block from
+    // one cursor (ctl->ncore ends as the number of core arcs; the order of
+    // the ranges is immaterial)
     const long long np = (long long)*(volatile u64 *)&ctl->npc;
-    const long long chunk = (np + gridDim.x - 1) / gridDim.x;
-    const long long lo = (long long)blockIdx.x * chunk, hi = lo + chunk < np ? lo + chunk : np;
-    {
-        long long sacc = 0;
-        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) sacc += LD(a.cdeg[i]);
-        long long tot;
-        block_excl_scan_ll(sacc, &tot);
-        if (threadIdx.x == 0) a.bsum[blockIdx.x] = tot;
-    }
-    if (!grid_barrier(ctl, bar)) return;
-    if (blockIdx.x == 0) {
-        long long nbk = gridDim.x;
-        long long per = (nbk + blockDim.x - 1) / blockDim.x;
-        long long l0 = threadIdx.x * per, l1 = l0 + per < nbk ? l0 + per : nbk;
-        long long sacc = 0;
-        for (long long i = l0; i < l1; ++i) sacc += LD(a.bsum[i]);
-        long long tot;
-        long long pre = block_excl_scan_ll(sacc, &tot);
-        for (long long i = l0; i < l1; ++i) {
-            long long t = LD(a.bsum[i]);
-            a.bsum[i] = pre;
-            pre += t;
-        }
-        if (threadIdx.x == 0) ctl->ncore = (u64)tot;   // core arcs = slots of the core adjacency
-    }
-    if (!grid_barrier(ctl, bar)) return;
-    {
-        long long carry = LD(a.bsum[blockIdx.x]);
-        for (long long t0 = lo; t0 < hi; t0 += blockDim.x) {
-            long long i = t0 + threadIdx.x;
-            long long d = i < hi ? LD(a.cdeg[i]) : 0;
-            long long tot;
-            long long pre = block_excl_scan_ll(d, &tot);
-            if (i < hi) a.poff[i] = (int)(carry + pre);
-            carry += tot;
-        }
+    for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < np; b0 += gstride()) {
+        const long long i = b0 + threadIdx.x;
+        const long long d = i < np ? LD(a.cdeg[i]) : 0;
+        const long long off = block_reserve(&ctl->ncore, d);
+        if (i < np) a.poff[i] = (int)off;
     }
     if (!grid_barrier(ctl, bar)) return;
     // phase 4: place core arcs in their source piece's adjacency
@@ -913,6 +959,10 @@ __global__ void k_active(const int *L, int use_list, long long cnt_static, Ctl *
 __global__ void k_mark(Ctl *ctl, const int *act, int *J0, int *J1, unsigned char *mark, const int *parent) {
     if (*(volatile int *)&ctl->skip) return;
     long long na = (long long)ctl->nact;
+    if (na == 0) {   // every path was walked (the same value in every block)
+        if (gtid() == 0) ctl->mark_rounds = 0;
+        return;
+    }
     int *Jc = J0, *Jn = J1;
     int r = 0;
     for (;; ++r) {
@@ -965,20 +1015,17 @@ __global__ void k_reverse(Ctl *ctl, const int *act, const int *pold, const unsig
                           const int *chy, int *parent) {
     if (*(volatile int *)&ctl->skip) return;
     long long na = (long long)ctl->nact, ner = (long long)ctl->ner;
+    long long c = 0;
     GS_LOOP(i, na) {
         int v = act[i];
         int p = pold[i];
-        if (mark[v] && p != v) parent[p] = v;
+        if (mark[v] && p != v) {
+            parent[p] = v;
+            ++c;
+        }
     }
-    GS_LOOP(i, ner) parent[chx[i]] = chy[i];
-}
-
-__global__ void k_count_reversed(Ctl *ctl, const int *act, const int *pold, const unsigned char *mark) {
-    if (*(volatile int *)&ctl->skip) return;
-    long long na = (long long)ctl->nact;
-    long long c = 0;
-    GS_LOOP(i, na) c += (mark[act[i]] && pold[i] != act[i]) ? 1 : 0;
     if (c) atomicAdd((u64 *)&ctl->reversed, (u64)c);
+    GS_LOOP(i, ner) parent[chx[i]] = chy[i];
 }
 
 // Component labels: smallest vertex id per tree (drsf_labels).
@@ -1051,9 +1098,11 @@ cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_
     return cudaLaunchCooperativeKernel((const void *)k_jump, d.coop_jump, BLK, args, 0, s);
 }
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
-                           int *comp, u64 *best0, u64 *best1, u64 *er, long long er_cap, cudaStream_t s) {
+                           int *comp, u64 *best0, u64 *best1, u64 *er, long long er_cap, unsigned *hstamp,
+                           cudaStream_t s) {
     void *args[] = {(void *)&ctl, (void *)&ck0, (void *)&ca0, (void *)&cb0, (void *)&ck1, (void *)&ca1,
-                    (void *)&cb1, (void *)&comp, (void *)&best0, (void *)&best1, (void *)&er, (void *)&er_cap};
+                    (void *)&cb1, (void *)&comp, (void *)&best0, (void *)&best1, (void *)&er, (void *)&er_cap,
+                    (void *)&hstamp};
     return cudaLaunchCooperativeKernel((const void *)k_boruvka, d.coop_hook, BLK, args, 0, s);
 }
 cudaError_t launch_orient(const Dev &d, Ctl *ctl, OrientArgs a, cudaStream_t s) {
@@ -1082,7 +1131,6 @@ cudaError_t launch_mark(const Dev &d, Ctl *ctl, const int *act, int *J0, int *J1
 }
 cudaError_t launch_reverse(const Dev &d, Ctl *ctl, const int *act, const int *pold, const unsigned char *mark,
                            const int *chx, const int *chy, int *parent, cudaStream_t s) {
-    k_count_reversed<<<d.grid, BLK, 0, s>>>(ctl, act, pold, mark);
     k_reverse<<<d.grid, BLK, 0, s>>>(ctl, act, pold, mark, chx, chy, parent);
     return cudaGetLastError();
 }

@@ -70,7 +70,8 @@ cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_
                         int *rep, RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g,
                         long long *bsum, int sync_rounds, int *X, int *Y, const int *cuts, cudaStream_t s);
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
-                           int *comp, u64 *best0, u64 *best1, u64 *er, long long er_cap, cudaStream_t s);
+                           int *comp, u64 *best0, u64 *best1, u64 *er, long long er_cap, unsigned *hstamp,
+                           cudaStream_t s);
 struct OrientArgs {
     const u64 *er;
     const int *rep;
