@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -177,27 +178,32 @@ def aggregate(units: float, seconds: float):
 # ------------------------------------------------------------ algorithmic bytes
 
 def phase_bytes(st: dict, n: int, op: int) -> dict:
-    """Algorithmic bytes per phase of one batch: each data item a phase must
-    touch, counted once per pass (see the design notes for the model)."""
+    """Algorithmic bytes per phase of one batch, from the batch's counters:
+    each data item the method must touch, counted once per pass, uncached
+    (per-unit figures: a0 24 per batch edge, a1 insert 16 + two 32-byte index
+    probes per applied edge, a1 delete two probes + an 8-byte tombstone, a2 4
+    per batch edge for the cut and 12 per affected vertex and doubling round,
+    a3 12 per scanned row + 8 per scanned entry + 8 per candidate and 24 per
+    candidate and hooking round, a4 64 r log2 r, a5 13 per active vertex and
+    marking round + 12 per reversed vertex, a6 8 per vertex of the pass)."""
     b, a = st["batch_len"], st["applied"]
     out = {"begin": 8 * b}
     if op == 0:
-        c = st["candidates"]
-        out["ins_claim"] = 8 * b + 8 * b + 16 * a
-        out["ins_place"] = 80 * a + 16 * c
-        out["active"] = 12 * n + 16 * st["active"]
+        out["ins_claim"] = 16 * b + 64 * a
+        out["ins_place"] = 16 * a + 8 * st["candidates"]
+        out["active"] = 8 * n
     else:
-        aff, det, sc, c = st["affected"], st["detached"], st["scanned"], st["candidates"]
-        out["del_claim"] = 8 * b + 40 * a + 12 * st["tree_cut"]
-        out["affected"] = 8 * n + 12 * aff
-        out["jump"] = 16 * st.get("jump_visits", aff * max(st["jump_rounds"], 1)) + 64 * aff + 4 * det
-        out["scan"] = 40 * det + 8 * sc + 32 * c
-        out["active"] = 16 * aff + 16 * st["active"]
+        aff = st["affected"]
+        out["del_claim"] = 16 * b + 72 * a + 4 * b
+        out["affected"] = 8 * n
+        out["jump"] = 12 * aff * max(st["jump_rounds"], 1)
+        out["scan"] = 12 * st["detached"] + 8 * st["scanned"] + 8 * st["candidates"]
+        out["active"] = 8 * aff
     c, ner = st["candidates"], st["replacement"]
-    out["hook"] = 80 * c + 16 * ner
-    out["orient"] = 120 * ner + 32 * ner * max(st["rank_rounds"], 1)
-    out["mark"] = 22 * st["active"] * max(st["mark_rounds"], 1)
-    out["reverse"] = 18 * st["active"] + 4 * st["reversed"] + 8 * ner
+    out["hook"] = 24 * c * max(st["hook_rounds"], 1)
+    out["orient"] = int(64 * ner * max(math.log2(max(ner, 2)), 1))
+    out["mark"] = 13 * st["active"] * st["mark_rounds"]
+    out["reverse"] = 12 * st["reversed"] + 8 * ner
     return out
 
 

@@ -265,6 +265,21 @@ __device__ __forceinline__ void block_reserve4(u64 *ctr, const bool f[4], long l
     __syncthreads();
 }
 
+// The same for two slabs.
+__device__ __forceinline__ void block_reserve2(u64 *ctr, const bool f[2], long long slot[2]) {
+    __shared__ u64 s_rb2;
+    long long packed = (long long)f[0] | ((long long)f[1] << 32);
+    long long tot;
+    long long pre = block_excl_scan_ll(packed, &tot);
+    long long t0 = tot & 0xFFFFFFFFll, t1 = tot >> 32;
+    if (threadIdx.x == 0) s_rb2 = t0 + t1 ? atomicAdd(ctr, (u64)(t0 + t1)) : 0;
+    __syncthreads();
+    long long base = (long long)s_rb2;
+    slot[0] = f[0] ? base + (pre & 0xFFFFFFFFll) : -1;
+    slot[1] = f[1] ? base + t0 + (pre >> 32) : -1;
+    __syncthreads();
+}
+
 // 64-bit minimum over a group of lanes (mask from __match_any_sync).
 __device__ __forceinline__ u64 group_min_u64(unsigned grp, u64 k) {
     unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;

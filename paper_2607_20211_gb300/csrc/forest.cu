@@ -23,6 +23,8 @@
 #define ORIENT_THREADS 1024
 // independent items per thread and iteration in the pointer-doubling rounds
 #define JU 4
+// the same for the final pass of the jump (more state per item)
+#define JF 2
 // consecutive items per thread in the list-building vertex passes
 #define IPT 4
 // longest path reversed by one walking thread (longer ones: doubling marks)
@@ -158,9 +160,6 @@ __device__ __forceinline__ void piece_count(int *s_wk, unsigned *s_wc, unsigned 
 // detaches most of a tree): then the heaviest piece.  The listed rows get an
 // exclusive prefix sum of their lengths in roff (roff[ndet] = total), their
 // CSR start and their (piece, piece left out) for the load-balanced scan.
-// In delete mode a vertex is settled in the round its pointer reaches a
-// root (no extra pass over the list): its representative, its piece's
-// weight and, outside the root piece, its entry in the provisional row list.
 // (6 blocks of BLK threads per SM: the rounds are latency-bound)
 __global__ void __launch_bounds__(BLK, 6)
     k_jump(const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1, int *rep, RowList rl, int mode,
@@ -182,15 +181,6 @@ __global__ void __launch_bounds__(BLK, 6)
         // either buffer see the root.
         int *Jc = J, *Jn = J1;
         int r = 0;
-        // piece-count table of the block (open addressing; counts go to
-        // global memory once per piece and block, or directly when the
-        // table has no slot)
-        __shared__ int s_wk[WT_SLOTS];
-        __shared__ unsigned s_wc[WT_SLOTS];
-        for (int t = threadIdx.x; t < WT_SLOTS; t += blockDim.x) {
-            s_wk[t] = -1;
-            s_wc[t] = 0;
-        }
         if (gtid() == 0) {
             ctl->cnt[0] = (u64)cnt;
             ctl->cnt[1] = 0;
@@ -213,7 +203,7 @@ __global__ void __launch_bounds__(BLK, 6)
             // are issued together (more loads in flight per thread)
             const long long S = gstride();
             for (long long base = (long long)blockIdx.x * blockDim.x; base < c; base += S * JU) {
-                int v[JU], w0[JU], w2[JU], ro[JU];
+                int v[JU], w0[JU], w2[JU];
                 bool ok[JU], open[JU];
 #pragma unroll
                 for (int k = 0; k < JU; ++k) {
@@ -222,12 +212,10 @@ __global__ void __launch_bounds__(BLK, 6)
                     v[k] = ok[k] ? (in ? in[i] : (int)i) : 0;
                 }
 #pragma unroll
-                for (int k = 0; k < JU; ++k) {
-                    w0[k] = ok[k] ? LD(Jc[v[k]]) : -1;
-                    ro[k] = (mode && ok[k]) ? rold[v[k]] : 0;
-                }
+                for (int k = 0; k < JU; ++k) w0[k] = ok[k] ? LD(Jc[v[k]]) : -1;
 #pragma unroll
                 for (int k = 0; k < JU; ++k) w2[k] = (ok[k] && w0[k] >= 0) ? LD(Jc[w0[k]]) : 0;
+                int nopen = 0;
 #pragma unroll
                 for (int k = 0; k < JU; ++k) {
                     open[k] = false;
@@ -239,52 +227,17 @@ __global__ void __launch_bounds__(BLK, 6)
                     else {
                         nv = w2[k];
                         open[k] = true;
+                        ++nopen;
                     }
                     Jn[v[k]] = nv;
                     if (!open[k]) Jc[v[k]] = nv;
-                    w0[k] = ~nv;   // the root once converged
                 }
+                (void)nopen;
                 long long q[JU];
                 block_reserve4(&ctl->cnt[(r + 1) % 3], open, q);
 #pragma unroll
                 for (int k = 0; k < JU; ++k)
                     if (open[k]) out[q[k]] = v[k];
-                if (!mode) continue;
-                // delete: a vertex is settled in the round it converges:
-                // its representative (written only when it left its tree's
-                // root piece), its piece's weight, and the provisional list
-                // of rows to scan (vertices outside the root piece)
-                bool scan[JU];
-#pragma unroll
-                for (int k = 0; k < JU; ++k) {
-                    w2[k] = 0;   // the row length of a listed vertex
-                    if (ok[k] && !open[k] && w0[k] != ro[k]) {
-                        rep[v[k]] = w0[k];
-                        int cap = (int)(g.off[v[k] + 1] - g.off[v[k]]);
-                        int used = g.used[v[k]];
-                        w2[k] = used < cap ? used : cap;
-                    }
-                    scan[k] = w2[k] > 0;
-                }
-#pragma unroll
-                for (int k = 0; k < JU; ++k) {
-                    bool settled = ok[k] && !open[k];
-                    unsigned vm = __ballot_sync(0xffffffffu, settled);
-                    if (settled) {
-                        unsigned grp = __match_any_sync(vm, w0[k]);
-                        if ((int)(threadIdx.x & 31) == __ffs(grp) - 1)
-                            piece_count(s_wk, s_wc, w, w0[k], (unsigned)__popc(grp));
-                    }
-                }
-                block_reserve4(&ctl->ndet, scan, q);
-#pragma unroll
-                for (int k = 0; k < JU; ++k)
-                    if (scan[k]) {
-                        D[q[k]] = v[k];
-                        roff[q[k]] = w2[k];
-                        rl.base[q[k]] = g.off[v[k]];
-                        rl.meta[q[k]] = make_int2(w0[k], ro[k]);
-                    }
             }
             if (!grid_barrier(ctl, &ctl->bar[0])) return;
             int *t = Jc; Jc = Jn; Jn = t;
@@ -297,7 +250,71 @@ __global__ void __launch_bounds__(BLK, 6)
             }
             return;
         }
-        // piece weights counted while settling
+        // final pass: representatives, piece weights (vertex counts; the
+        // weight slots of piece roots were zeroed at the cut) and a
+        // provisional list of rows to scan: every vertex outside its tree's
+        // root piece (only those read their row length).  JU vertices per
+        // thread and iteration.  Piece counts go to a small open-addressing
+        // table in shared memory (one global atomic per piece and block at
+        // the end; a large piece spans many blocks), or straight to global
+        // memory when the table has no slot.
+        __shared__ int s_wk[WT_SLOTS];
+        __shared__ unsigned s_wc[WT_SLOTS];
+        for (int t = threadIdx.x; t < WT_SLOTS; t += blockDim.x) {
+            s_wk[t] = -1;
+            s_wc[t] = 0;
+        }
+        __syncthreads();
+        const long long S = gstride();
+        for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += S * JF) {
+            int v[JF], p[JF], ro[JF], len[JF];
+            bool ok[JF], scan[JF];
+#pragma unroll
+            for (int k = 0; k < JF; ++k) {
+                long long i = base + k * S + threadIdx.x;
+                ok[k] = i < cnt;
+                v[k] = ok[k] ? A[i] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < JF; ++k) {
+                p[k] = ok[k] ? ~LD(Jc[v[k]]) : 0;
+                ro[k] = ok[k] ? rold[v[k]] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < JF; ++k) {
+                scan[k] = false;
+                len[k] = 0;
+                if (!ok[k]) continue;
+                // rep[v] == rold[v] already for the root piece's vertices
+                if (p[k] != ro[k]) {
+                    rep[v[k]] = p[k];
+                    int cap = (int)(g.off[v[k] + 1] - g.off[v[k]]);
+                    int used = g.used[v[k]];
+                    len[k] = used < cap ? used : cap;
+                    scan[k] = len[k] > 0;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < JF; ++k) {
+                unsigned vm = __ballot_sync(0xffffffffu, ok[k]);
+                if (ok[k]) {
+                    unsigned grp = __match_any_sync(vm, p[k]);
+                    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
+                        piece_count(s_wk, s_wc, w, p[k], (unsigned)__popc(grp));
+                    }
+                }
+            }
+            long long q[JF];
+            block_reserve2(&ctl->ndet, scan, q);
+#pragma unroll
+            for (int k = 0; k < JF; ++k)
+                if (scan[k]) {
+                    D[q[k]] = v[k];
+                    roff[q[k]] = len[k];
+                    rl.base[q[k]] = g.off[v[k]];
+                    rl.meta[q[k]] = make_int2(p[k], ro[k]);
+                }
+        }
         __syncthreads();
         for (int t = threadIdx.x; t < WT_SLOTS; t += blockDim.x)
             if (s_wk[t] != -1) atomicAdd(&w[s_wk[t]], s_wc[t]);
