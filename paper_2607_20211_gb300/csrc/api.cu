@@ -57,8 +57,10 @@ struct drsf_ctx {
     u64 *best0 = nullptr, *best1 = nullptr, *er = nullptr, *heavy = nullptr;
     int *rold = nullptr, *cdeg = nullptr, *xlist = nullptr, *aidx = nullptr, *aroot = nullptr;
     int *oep = nullptr, *oeid = nullptr, *oeroot = nullptr;
-    long long *roff = nullptr, *rbase = nullptr;
+    unsigned *roff = nullptr, *rbase = nullptr;
     int2 *rmeta = nullptr;
+    int *tile = nullptr;          // row of each 32-entry tile of the scanned rows
+    long long tile_cap = 0;
     unsigned char *lf = nullptr;
     unsigned *wgt = nullptr;
     PairTable pt{};
@@ -114,7 +116,7 @@ static const char *kPhaseNames[DRSF_NUM_PHASES] = {
     "begin", "ins_claim", "ins_place", "del_claim", "affected", "jump", "scan", "hook", "orient", "active",
     "mark", "reverse"};
 
-static RowList rows(drsf_ctx *h) { return RowList{h->D, h->roff, h->rbase, h->rmeta}; }
+static RowList rows(drsf_ctx *h) { return RowList{h->D, h->roff, h->rbase, h->rmeta, h->tile}; }
 
 static void prof_begin(drsf_ctx *h, int phase, cudaStream_t s) {
     if (!h->prof_on || 2 * (h->prof_used + 1) > h->prof_ev.size()) return;
@@ -256,6 +258,13 @@ static drsf_status build_graph(drsf_ctx *h, const int *edges, long long m, cudaS
             CKA(halloc(h, &h->cb[b], need, s));
         }
         h->cand_cap = need;
+    }
+    // tiles of the scanned rows: at most one per 32 CSR slots, plus one
+    const long long ntile = total / 32 + 2;
+    if (ntile > h->tile_cap) {
+        hfree(h, &h->tile, s);
+        CKA(halloc(h, &h->tile, (size_t)ntile, s));
+        h->tile_cap = ntile;
     }
     CK(cudaStreamSynchronize(s));
     // swap in
@@ -506,10 +515,9 @@ static drsf_status create_impl(drsf_ctx *h, const int32_t *edges, int64_t m, con
     if (st) return st;
     CK(cudaMemcpyAsync(h->parent, parent, (size_t)n * sizeof(int), cudaMemcpyDeviceToDevice, s));
     // representatives of F by pointer jumping over all vertices
-    CK(launch_copy_parent(n, h->parent, h->J0, s));
     Csr g0{h->off, h->used, h->col};
-    CK(launch_jump(h->dev, nullptr, 0, n, h->ctl, h->J0, h->J1, h->rep, rows(h), 0, h->rold, h->wgt, h->heavy, g0,
-                   h->bsum, h->jump_sync, h->act, h->xlist, h->cutlist, s));
+    CK(launch_jump(h->dev, nullptr, 0, n, h->ctl, h->parent, h->J0, h->J1, h->rep, rows(h), 0, h->rold, h->wgt,
+                   h->heavy, g0, h->bsum, h->jump_sync, h->act, h->xlist, h->cutlist, s));
     Ctl c{};
     CK(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -573,6 +581,7 @@ drsf_status drsf_create(int32_t n, const int32_t *edges, int64_t m, const int32_
     h->dev.coop_orient = coop_blocks_orient(nsm);
     h->dev.coop_mark = coop_blocks_mark(nsm);
     h->dev.coop_bfs = coop_blocks_bfs(nsm);
+    h->dev.grid_scan = scan_grid(nsm);
     h->dev.coop_et = coop_blocks_et(nsm);
     // DRSF_JUMP=halving selects the in-place path-halving root search
     const char *jm = getenv("DRSF_JUMP");
@@ -618,12 +627,11 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
                             h->cutlist, h->wgt, s));
         prof_end(h, PH_DEL_CLAIM, len > 0 ? 1 : 0, s);
         prof_begin(h, PH_AFF, s);
-        CK(launch_aff_collect(h->dev, h->n, h->rep, h->aff_ep, h->parent, h->J0, h->A, h->rold, h->wgt, h->heavy,
-                              ctl, s));
+        CK(launch_aff_collect(h->dev, h->n, h->rep, h->aff_ep, h->A, h->rold, h->wgt, h->heavy, ctl, s));
         prof_end(h, PH_AFF, 1, s);
         prof_begin(h, PH_JUMP, s);
-        CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->J0, h->J1, h->rep, rows(h), 1, h->rold, h->wgt, h->heavy, g,
-                       h->bsum, h->jump_sync, h->act, h->xlist, h->cutlist, s));
+        CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->parent, h->J0, h->J1, h->rep, rows(h), 1, h->rold, h->wgt,
+                       h->heavy, g, h->bsum, h->jump_sync, h->act, h->xlist, h->cutlist, s));
         prof_end(h, PH_JUMP, 1, s);
         prof_begin(h, PH_SCAN, s);
         CK(launch_scan_rows(h->dev, rows(h), ctl, g, h->rep, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));

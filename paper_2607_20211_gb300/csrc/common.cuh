@@ -138,6 +138,21 @@ __device__ __forceinline__ void warp_atomic_min_u64(u64 *arr, int idx, u64 k, bo
 // pieces.  Probing is bounded; a pair that finds no slot returns false and
 // the caller keeps the edge as a plain candidate instead.
 #define PAIR_PROBES 64
+// Slot of a piece pair key (claimed if absent), or -1 when the probes found
+// no slot.
+__device__ __forceinline__ long long pair_slot(u64 *pk, u64 mask, u64 pair) {
+    u64 s = hslot(pair, mask);
+    for (int p = 0; p < PAIR_PROBES; ++p) {
+        u64 cur = __ldcg(&pk[s]);
+        if (cur == pair) return (long long)s;
+        if (cur == EMPTY_KEY) {
+            u64 old = atomicCAS(&pk[s], EMPTY_KEY, pair);
+            if (old == EMPTY_KEY || old == pair) return (long long)s;
+        }
+        s = (s + 1) & mask;
+    }
+    return -1;
+}
 __device__ __forceinline__ bool pair_min(u64 *pk, u64 *mk, u64 mask, int a, int b, u64 key) {
     u64 pair = a < b ? ((u64)(unsigned)a << 32) | (unsigned)b : ((u64)(unsigned)b << 32) | (unsigned)a;
     u64 s = hslot(pair, mask);

@@ -78,12 +78,12 @@ __global__ void k_begin(Ctl *ctl, int op, long long len) {
 }
 
 // Delete: list the vertices of every tree that lost a tree edge (its old
-// root was stamped by the cut) and seed J0 = parent (the cut forest F^).
+// root was stamped by the cut), with their old root.
 // Each thread takes IPT consecutive vertices per iteration (one vector load
 // of rep, IPT gathers in flight) and the block reserves its list slots with
 // one atomic; the list stays in vertex order.
-__global__ void k_aff_collect(int n, const int *rep, const unsigned *aff_ep, const int *parent, int *J0, int *A,
-                              int *rold, unsigned *w, u64 *heavy, Ctl *ctl) {
+__global__ void k_aff_collect(int n, const int *rep, const unsigned *aff_ep, int *A, int *rold, unsigned *w,
+                              u64 *heavy, Ctl *ctl) {
     if (*(volatile int *)&ctl->skip) return;
     unsigned ep = ctl->epoch;
     const long long step = (long long)gridDim.x * blockDim.x * IPT;
@@ -104,7 +104,6 @@ __global__ void k_aff_collect(int n, const int *rep, const unsigned *aff_ep, con
             if (!in[k]) continue;
             const int v = (int)(v0 + k);
             A[p++] = v;
-            J0[v] = parent[v];
             rold[v] = r[k];
             if (r[k] == v) {   // the old root: piece-weight and heaviest-piece slots
                 w[v] = 0;
@@ -112,10 +111,6 @@ __global__ void k_aff_collect(int n, const int *rep, const unsigned *aff_ep, con
             }
         }
     }
-}
-
-__global__ void k_copy(int n, const int *src, int *dst) {
-    GS_LOOP(v, n) dst[v] = src[v];
 }
 
 // Root of v in the forest J by pointer jumping with path halving, in place:
@@ -151,6 +146,12 @@ __device__ __forceinline__ void piece_count(int *s_wk, unsigned *s_wc, unsigned 
     atomicAdd(&w[p], cnt);
 }
 
+// tile[T] = row for the tiles of 32 entries whose first entry lies in the
+// row of entries [st, st + d), d > 0 (rows are never empty)
+__device__ __noinline__ void fill_tiles(int *tile, long long st, long long d, int row) {
+    for (long long T = (st + 31) >> 5; T <= (st + d - 1) >> 5; ++T) tile[T] = row;
+}
+
 // Representatives (Algorithm 1, parallel pointer jumping) of the listed
 // vertices: rep[v] = root of v in F^ (J starts as a copy of parent).
 // Delete mode (1) then chooses the rows to scan for cross edges: every cross
@@ -162,11 +163,11 @@ __device__ __forceinline__ void piece_count(int *s_wk, unsigned *s_wc, unsigned 
 // CSR start and their (piece, piece left out) for the load-balanced scan.
 // (6 blocks of BLK threads per SM: the rounds are latency-bound)
 __global__ void __launch_bounds__(BLK, 6)
-    k_jump(const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1, int *rep, RowList rl, int mode,
-           const int *rold, unsigned *w, u64 *heavy, Csr g, long long *bsum, int sync_rounds, int *X, int *Y,
-           const int *cuts) {
+    k_jump(const int *A, int use_list, long long cnt_static, Ctl *ctl, const int *par, int *J, int *J1, int *rep,
+           RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g, long long *bsum, int sync_rounds,
+           int *X, int *Y, const int *cuts) {
     int *const D = rl.D;
-    long long *const roff = rl.roff;
+    unsigned *const roff = rl.roff;
     if (*(volatile int *)&ctl->skip) return;
     long long cnt = use_list ? (long long)ctl->naff : cnt_static;
     if (sync_rounds) {
@@ -178,7 +179,8 @@ __global__ void __launch_bounds__(BLK, 6)
         // round 0) and appends the ones still open after it to the other
         // work list (X, Y alternate); a vertex that converges writes its
         // complemented root into both buffers, so later reads of it from
-        // either buffer see the root.
+        // either buffer see the root.  Round 0 reads the forest itself
+        // (par); its converged vertices still write both buffers.
         int *Jc = J, *Jn = J1;
         int r = 0;
         if (gtid() == 0) {
@@ -211,11 +213,11 @@ __global__ void __launch_bounds__(BLK, 6)
                     ok[k] = i < c;
                     v[k] = ok[k] ? (in ? in[i] : (int)i) : 0;
                 }
+                const int *Jr = r == 0 ? par : Jc;
 #pragma unroll
-                for (int k = 0; k < JU; ++k) w0[k] = ok[k] ? LD(Jc[v[k]]) : -1;
+                for (int k = 0; k < JU; ++k) w0[k] = ok[k] ? LD(Jr[v[k]]) : -1;
 #pragma unroll
-                for (int k = 0; k < JU; ++k) w2[k] = (ok[k] && w0[k] >= 0) ? LD(Jc[w0[k]]) : 0;
-                int nopen = 0;
+                for (int k = 0; k < JU; ++k) w2[k] = (ok[k] && w0[k] >= 0) ? LD(Jr[w0[k]]) : 0;
 #pragma unroll
                 for (int k = 0; k < JU; ++k) {
                     open[k] = false;
@@ -227,12 +229,10 @@ __global__ void __launch_bounds__(BLK, 6)
                     else {
                         nv = w2[k];
                         open[k] = true;
-                        ++nopen;
                     }
                     Jn[v[k]] = nv;
                     if (!open[k]) Jc[v[k]] = nv;
                 }
-                (void)nopen;
                 long long q[JU];
                 block_reserve4(&ctl->cnt[(r + 1) % 3], open, q);
 #pragma unroll
@@ -310,8 +310,8 @@ __global__ void __launch_bounds__(BLK, 6)
             for (int k = 0; k < JF; ++k)
                 if (scan[k]) {
                     D[q[k]] = v[k];
-                    roff[q[k]] = len[k];
-                    rl.base[q[k]] = g.off[v[k]];
+                    roff[q[k]] = (unsigned)len[k];
+                    rl.base[q[k]] = (unsigned)g.off[v[k]];
                     rl.meta[q[k]] = make_int2(p[k], ro[k]);
                 }
         }
@@ -321,6 +321,11 @@ __global__ void __launch_bounds__(BLK, 6)
     } else {
         // J[v] may later be overwritten by another walk's halving step with
         // a non-root ancestor; rep[v] takes this thread's own result.
+        for (long long i = gtid(); i < cnt; i += gstride()) {
+            int v = use_list ? A[i] : (int)i;
+            J[v] = par[v];
+        }
+        if (!grid_barrier(ctl, &ctl->bar[0])) return;
         for (long long i = gtid(); i < cnt; i += gstride()) {
             int v = use_list ? A[i] : (int)i;
             int root = find_halving(J, v, ctl);
@@ -390,8 +395,8 @@ __global__ void __launch_bounds__(BLK, 6)
             long long q = block_append(&ctl->ndet, scan);
             if (scan) {
                 D[q] = v;
-                roff[q] = len;
-                rl.base[q] = g.off[v];
+                roff[q] = (unsigned)len;
+                rl.base[q] = (unsigned)g.off[v];
                 rl.meta[q] = make_int2(pv, hp);
             }
         }
@@ -423,7 +428,7 @@ __global__ void __launch_bounds__(BLK, 6)
             bsum[i] = pre;
             pre += t;
         }
-        if (threadIdx.x == 0) roff[nd] = tot;
+        if (threadIdx.x == 0) roff[nd] = (unsigned)tot;
     }
     if (!grid_barrier(ctl, &ctl->bar[0])) return;
     {
@@ -433,7 +438,11 @@ __global__ void __launch_bounds__(BLK, 6)
             long long d = i < hi ? LD(roff[i]) : 0;
             long long tot;
             long long pre = block_excl_scan_ll(d, &tot);
-            if (i < hi) roff[i] = carry + pre;
+            if (i < hi) {
+                const long long st = carry + pre;
+                roff[i] = (unsigned)st;
+                fill_tiles(rl.tile, st, d, (int)i);
+            }
             carry += tot;
         }
     }
@@ -928,21 +937,26 @@ __global__ void k_active(const int *L, int use_list, long long cnt_static, Ctl *
     for (long long b0 = (long long)blockIdx.x * blockDim.x * IPT; b0 < cnt; b0 += step) {
         const long long i0 = b0 + (long long)threadIdx.x * IPT;
         int v[IPT], p[IPT], x[IPT];
-        bool on[IPT];
+        bool on[IPT], chg[IPT];
         if (use_list) {
             load_ipt(L, i0, cnt, v);
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) p[k] = i0 + k < cnt ? rep[v[k]] : 0;
         } else {
 #pragma unroll
             for (int k = 0; k < IPT; ++k) v[k] = (int)(i0 + k);
+            load_ipt(rep, i0, cnt, p);
         }
+        // the pieces selected for the marks are re-rooted child pieces, all
+        // of which get a new representative: one gather in the common case
 #pragma unroll
-        for (int k = 0; k < IPT; ++k) p[k] = i0 + k < cnt ? rep[v[k]] : 0;
+        for (int k = 0; k < IPT; ++k) chg[k] = i0 + k < cnt && rep_ep[p[k]] == ep;
         int c = 0;
 #pragma unroll
         for (int k = 0; k < IPT; ++k) {
             on[k] = false;
             x[k] = -1;
-            if (i0 + k < cnt && sel_ep[p[k]] == ep) {
+            if (chg[k] && sel_ep[p[k]] == ep) {
                 x[k] = att_x[p[k]];
                 on[k] = x[k] != p[k];
             }
@@ -962,7 +976,7 @@ __global__ void k_active(const int *L, int use_list, long long cnt_static, Ctl *
                 aroot[q] = p[k];       // the piece root
                 ++q;
             }
-            if (rep_ep[p[k]] == ep) rep[v[k]] = newrep[p[k]];
+            if (chg[k]) rep[v[k]] = newrep[p[k]];
         }
     }
 }
@@ -1096,22 +1110,19 @@ cudaError_t launch_begin(Ctl *ctl, int op, long long len, cudaStream_t s) {
     k_begin<<<1, 32, 0, s>>>(ctl, op, len);
     return cudaGetLastError();
 }
-cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, const int *parent,
-                               int *J0, int *A, int *rold, unsigned *w, u64 *heavy, Ctl *ctl, cudaStream_t s) {
-    k_aff_collect<<<gsz((n + IPT - 1) / IPT), BLK, 0, s>>>(n, rep, aff_ep, parent, J0, A, rold, w, heavy, ctl);
+cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, int *A, int *rold,
+                               unsigned *w, u64 *heavy, Ctl *ctl, cudaStream_t s) {
+    k_aff_collect<<<gsz((n + IPT - 1) / IPT), BLK, 0, s>>>(n, rep, aff_ep, A, rold, w, heavy, ctl);
     (void)d;
     return cudaGetLastError();
 }
-cudaError_t launch_copy_parent(int n, const int *parent, int *J0, cudaStream_t s) {
-    k_copy<<<gsz(n), BLK, 0, s>>>(n, parent, J0);
-    return cudaGetLastError();
-}
-cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1,
-                        int *rep, RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g,
-                        long long *bsum, int sync_rounds, int *X, int *Y, const int *cuts, cudaStream_t s) {
-    void *args[] = {(void *)&A, (void *)&use_list, (void *)&cnt_static, (void *)&ctl, (void *)&J, (void *)&J1,
-                    (void *)&rep, (void *)&rl, (void *)&mode, (void *)&rold, (void *)&w, (void *)&heavy,
-                    (void *)&g, (void *)&bsum, (void *)&sync_rounds, (void *)&X, (void *)&Y, (void *)&cuts};
+cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, const int *par,
+                        int *J, int *J1, int *rep, RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy,
+                        Csr g, long long *bsum, int sync_rounds, int *X, int *Y, const int *cuts, cudaStream_t s) {
+    void *args[] = {(void *)&A, (void *)&use_list, (void *)&cnt_static, (void *)&ctl, (void *)&par, (void *)&J,
+                    (void *)&J1, (void *)&rep, (void *)&rl, (void *)&mode, (void *)&rold, (void *)&w,
+                    (void *)&heavy, (void *)&g, (void *)&bsum, (void *)&sync_rounds, (void *)&X, (void *)&Y,
+                    (void *)&cuts};
     return cudaLaunchCooperativeKernel((const void *)k_jump, d.coop_jump, BLK, args, 0, s);
 }
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,

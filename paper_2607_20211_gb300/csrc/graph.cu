@@ -223,6 +223,17 @@ __global__ void k_ins_claim(const int *batch, long long len, Index ix, Ctl *ctl,
     block_add(&ctl->dropped, drops);
 }
 
+// One slot of row r's append cursor per calling lane; lanes of a warp with
+// the same row share one atomicAdd.
+__device__ __forceinline__ int row_slot(int *used, int r) {
+    const unsigned grp = __match_any_sync(__activemask(), r);
+    const int lane = threadIdx.x & 31, ld = __ffs(grp) - 1;
+    int base = 0;
+    if (lane == ld) base = atomicAdd(&used[r], __popc(grp));
+    base = __shfl_sync(grp, base, ld);
+    return base + __popc(grp & ((1u << lane) - 1u));
+}
+
 // Insert, step 2: append each new edge to both CSR rows (warp-aggregated
 // row cursors are per row, so plain atomics); an edge whose row is full goes
 // whole to the overflow list.  The cross test of the insert case (M = B,
@@ -243,7 +254,9 @@ __global__ void k_ins_place(const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, 
             uint32_t a = klo(k), b = khi(k);
             long long oa = g.off[a], ob = g.off[b];
             long long capa = g.off[a + 1] - oa, capb = g.off[b + 1] - ob;
-            int pa = atomicAdd(&g.used[a], 1), pb = atomicAdd(&g.used[b], 1);
+            // lanes appending to the same row take consecutive slots from one
+            // atomic (a hub row receives many of a batch's edges)
+            int pa = row_slot(g.used, (int)a), pb = row_slot(g.used, (int)b);
             bool fa = pa < capa, fb = pb < capb;
             if (fa && fb) {
                 g.col[oa + pa] = (int)b;
@@ -348,94 +361,95 @@ __global__ void k_del_claim(const int *batch, long long len, Index ix, Csr g, u6
 
 // Delete, cross-edge scan (key edges M = E(G) - E(F) - B, Algorithm 1,
 // restricted).  The rows of the listed vertices (every vertex outside the
-// piece left out of its cut tree) are flattened by the prefix sum roff, and
-// each warp takes 32 consecutive entries, whatever rows they fall in (load
-// balanced: a hub row is spread over many warps, short rows share a warp).
-// The warp loads the list entries of the 32 rows starting at the row of its
-// first entry (one coalesced load per field), and lane e takes its row's
-// fields from the lane that loaded them, so an entry costs one column load
-// and one rep gather after the window.  A live neighbour x of u in another
-// piece gives the cross edge {u, x}; every cross edge has a listed endpoint
-// and, when both are listed, the smaller id emits it.  Parallel edges
-// between two pieces are reduced to the one with the minimum key, which is
-// the only one that can be in the minimum spanning forest: lanes holding the
-// same piece pair take the minimum first, then one lane updates the pair
-// table.  A pair that finds no table slot is emitted as a plain candidate.
+// piece left out of its cut tree) are flattened by the prefix sum roff and
+// cut into tiles of 32 entries, whatever rows they fall in (load balanced:
+// a hub row is spread over many warps, short rows share a tile); each warp
+// takes a contiguous range of tiles.  For a tile the warp loads the list
+// entries of the 32 rows starting at the tile's first row (one coalesced
+// load per field) and lane e takes its row's fields from the lane that
+// loaded them, so an entry costs one column load and one rep gather.  A
+// live neighbour x of u in another piece gives the cross edge {u, x}; every
+// cross edge has a listed endpoint and, when both are listed, the smaller
+// id emits it.  Parallel edges between two pieces are reduced to the one
+// with the minimum key, which is the only one that can be in the minimum
+// spanning forest: lanes holding the same piece pair take the minimum
+// first, then one lane updates the pair table.  A pair that finds no table
+// slot is emitted as a plain candidate.  Entry positions are below 2^32, so
+// the tile arithmetic is 32-bit.
 __global__ void k_scan_lb(RowList rl, Ctl *ctl, Csr g, const int *rep, PairTable pt, u64 *ck, int *ca, int *cb,
                           u64 cand_cap) {
     if (*(volatile int *)&ctl->skip) return;
-    const long long nd = (long long)ctl->ndet;
+    const unsigned nd = (unsigned)ctl->ndet;
     if (nd == 0) return;
-    const long long *roff = rl.roff;
-    const long long E = roff[nd];
+    const unsigned E = rl.roff[nd];
+    const unsigned NT = (E + 31) >> 5;
     const int lane = threadIdx.x & 31;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned warp = (unsigned)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const unsigned nw = (unsigned)((gridDim.x * blockDim.x) >> 5);
     if (warp == 0 && lane == 0) atomicAdd((u64 *)&ctl->scanned, (u64)E);
-    // this warp's contiguous range of entries, whole tiles of 32
-    const long long per = ((E + nw - 1) / nw + 31) & ~31ll;
-    const long long e_lo = warp * per, e_hi = e_lo + per < E ? e_lo + per : E;
-    if (e_lo >= e_hi) return;
-    long long r0 = 0;
-    if (lane == 0) {
-        long long lo = 0, hi = nd - 1;
-        while (lo < hi) {
-            long long mid = (lo + hi + 1) >> 1;
-            if (roff[mid] <= e_lo) lo = mid;
-            else hi = mid - 1;
-        }
-        r0 = lo;
-    }
-    r0 = __shfl_sync(0xffffffffu, r0, 0);
-    for (long long t0 = e_lo; t0 < e_hi; t0 += 32) {
-        const long long e = t0 + lane;
-        // window: rows r0 .. r0+31 (start wv, vertex, CSR start, pieces)
-        const long long wr = r0 + lane;
+    const unsigned per = (NT + nw - 1) / nw;
+    const unsigned t_lo = warp * per, t_hi = t_lo + per < NT ? t_lo + per : NT;
+    // the pair-table slot this lane used last (a hub row repeats one piece
+    // pair over many tiles: no probe for it)
+    u64 cpair = EMPTY_KEY, cslot = 0;
+    for (unsigned T = t_lo; T < t_hi; ++T) {
+        const unsigned t0 = T << 5;
+        // window: rows r0 .. r0+31 from the tile's first row
+        const unsigned wr = (unsigned)rl.tile[T] + lane;
         const bool wok = wr < nd;
-        const long long wv = wok ? roff[wr] : LLONG_MAX;
+        const unsigned wv = wok ? rl.roff[wr] : 0xFFFFFFFFu;
         const int wu = wok ? rl.D[wr] : 0;
-        const long long wb = wok ? rl.base[wr] : 0;
+        const unsigned wb = wok ? rl.base[wr] : 0;
         const int2 wm = wok ? rl.meta[wr] : make_int2(0, 0);
-        // the rows after r0 that start inside this tile set a bit at their
-        // start position; the row of position q is r0 plus the number of
-        // such starts at positions <= q
-        const long long pos = wv - t0;
-        const unsigned bit = (lane > 0 && pos >= 0 && pos < 32) ? (1u << pos) : 0u;
+        // the rows after the first that start inside this tile set a bit at
+        // their start position (a row that starts before the tile wraps to
+        // a large offset); the row of position p is the first row plus the
+        // number of such starts at positions <= p
+        const unsigned pos = wv - t0;
+        const unsigned bit = (lane > 0 && pos < 32) ? (1u << pos) : 0u;
         const unsigned starts = __reduce_or_sync(0xffffffffu, bit);
         const int c = __popc(starts & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u)));
         // all lanes take part in the shuffles
-        const long long rstart = __shfl_sync(0xffffffffu, wv, c);
+        const unsigned rstart = __shfl_sync(0xffffffffu, wv, c);
         const int u = __shfl_sync(0xffffffffu, wu, c);
-        const long long rb = __shfl_sync(0xffffffffu, wb, c);
+        const unsigned rb = __shfl_sync(0xffffffffu, wb, c);
         const int ru = __shfl_sync(0xffffffffu, wm.x, c);
         const int hp = __shfl_sync(0xffffffffu, wm.y, c);
-        // the next tile starts at t0 + 32: in the row of this tile's last
-        // entry or the one after it (rows are never empty); the window of
-        // the next tile must start exactly at that row
-        {
-            const int c31 = __shfl_sync(0xffffffffu, c, 31);
-            long long nstart = __shfl_sync(0xffffffffu, wv, c31 < 31 ? c31 + 1 : 31);
-            if (c31 == 31) nstart = r0 + 32 < nd ? roff[r0 + 32] : LLONG_MAX;
-            r0 += c31 + (nstart <= t0 + 32 ? 1 : 0);
-        }
-        bool emit = false;
-        int x = -1, rx = 0;
-        if (e < e_hi) {
-            x = __ldcs(&g.col[rb + (e - rstart)]);
-            if (x >= 0) {
-                rx = rep[x];
-                if (rx != ru) emit = rx == hp || u < x;
-            }
-        }
-        unsigned m = __ballot_sync(0xffffffffu, emit);
+        const unsigned e = t0 + lane;
+        const int x = e < E ? __ldcs(&g.col[(size_t)(rb + (e - rstart))]) : -1;
+        const int rx = x >= 0 ? rep[x] : 0;
+        const bool emit = x >= 0 && rx != ru && (rx == hp || u < x);
+        const unsigned m = __ballot_sync(0xffffffffu, emit);
+        if (!m) continue;
         bool raw = false;
         u64 key = 0;
         if (emit) {
-            unsigned grp = __match_any_sync(m, ((u64)(unsigned)ru << 32) | (unsigned)rx);
+            // one piece pair for the whole warp is the common case (a hub
+            // row against one other piece): no match needed then
+            const int ld = __ffs(m) - 1;
+            const int lru = __shfl_sync(m, ru, ld), lrx = __shfl_sync(m, rx, ld);
+            const unsigned grp = __all_sync(m, ru == lru && rx == lrx)
+                                     ? m
+                                     : __match_any_sync(m, ((u64)(unsigned)ru << 32) | (unsigned)rx);
             key = group_min_u64(grp, ekey((uint32_t)u, (uint32_t)x));
-            if (lane == __ffs(grp) - 1) raw = !pair_min(pt.pk, pt.mk, pt.mask, ru, rx, key);
+            if (lane == __ffs(grp) - 1) {
+                const u64 pair = ru < rx ? ((u64)(unsigned)ru << 32) | (unsigned)rx
+                                         : ((u64)(unsigned)rx << 32) | (unsigned)ru;
+                if (pair == cpair) {
+                    atomicMin(&pt.mk[cslot], key);
+                } else {
+                    const long long sl = pair_slot(pt.pk, pt.mask, pair);
+                    if (sl >= 0) {
+                        atomicMin(&pt.mk[sl], key);
+                        cpair = pair;
+                        cslot = (u64)sl;
+                    } else {
+                        raw = true;
+                    }
+                }
+            }
         }
-        long long p = agg_append(&ctl->ncand, raw);
+        const long long p = agg_append(&ctl->ncand, raw);
         if (raw) {
             if ((u64)p < cand_cap) {
                 ck[p] = key;
@@ -639,8 +653,16 @@ cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u
 }
 cudaError_t launch_scan_rows(const Dev &d, RowList rl, Ctl *ctl, Csr g, const int *rep, PairTable pt, u64 *ck,
                              int *ca, int *cb, u64 cand_cap, cudaStream_t s) {
-    k_scan_lb<<<d.grid, BLK, 0, s>>>(rl, ctl, g, rep, pt, ck, ca, cb, cand_cap);
+    k_scan_lb<<<d.grid_scan, BLK, 0, s>>>(rl, ctl, g, rep, pt, ck, ca, cb, cand_cap);
     return cudaGetLastError();
+}
+// Every warp of the row scan takes an equal share of the tiles, so the grid
+// is exactly the blocks that are resident at once (no second wave).
+unsigned scan_grid(int nsm) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k_scan_lb, BLK, 0) != cudaSuccess || per < 1)
+        per = 1;
+    return (unsigned)(per * nsm);
 }
 cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, PairTable pt, u64 *ck, int *ca,
                             int *cb, u64 cand_cap, cudaStream_t s) {

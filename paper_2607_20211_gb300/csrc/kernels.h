@@ -16,9 +16,11 @@ struct Dev {
     unsigned coop_mark;
     unsigned coop_bfs;
     unsigned coop_et;
+    unsigned grid_scan;   // row scan: the co-resident block count
 };
 
 // graph.cu -------------------------------------------------------------
+unsigned scan_grid(int nsm);
 cudaError_t launch_check_range(const int *a, long long cnt, int n, int *bad, cudaStream_t s);
 cudaError_t launch_create_claim(const int *edges, long long m, Index ix, u64 *dkey, u64 *dslot, u64 *cnt,
                                 long long *self_loops, cudaStream_t s);
@@ -38,12 +40,14 @@ cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u
 // The rows a delete batch scans for cross edges, one entry per listed
 // vertex u: u itself, the exclusive prefix sum of the row lengths (roff[nd]
 // = total), the row's start in the CSR, and (rep[u], piece left out of the
-// scan in u's tree).
+// scan in u's tree); and for each tile of 32 consecutive entries of the
+// flattened rows, the row of its first entry.
 struct RowList {
     int *D;
-    long long *roff;
-    long long *base;
+    unsigned *roff;   // entry counts and CSR positions are below 2^32
+    unsigned *base;   // (checked at build)
     int2 *meta;
+    int *tile;        // tile[T] = the row holding entry 32 T (tiles of 32 entries)
 };
 struct PairTable {
     u64 *pk;   // piece pair key, EMPTY_KEY when free
@@ -63,12 +67,11 @@ cudaError_t launch_check_cross(const int *pairs, long long m, const int *rep, in
 
 // forest.cu ------------------------------------------------------------
 cudaError_t launch_begin(Ctl *ctl, int op, long long len, cudaStream_t s);
-cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, const int *parent,
-                               int *J0, int *A, int *rold, unsigned *w, u64 *heavy, Ctl *ctl, cudaStream_t s);
-cudaError_t launch_copy_parent(int n, const int *parent, int *J0, cudaStream_t s);
-cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, int *J, int *J1,
-                        int *rep, RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g,
-                        long long *bsum, int sync_rounds, int *X, int *Y, const int *cuts, cudaStream_t s);
+cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, int *A, int *rold,
+                               unsigned *w, u64 *heavy, Ctl *ctl, cudaStream_t s);
+cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, const int *par,
+                        int *J, int *J1, int *rep, RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy,
+                        Csr g, long long *bsum, int sync_rounds, int *X, int *Y, const int *cuts, cudaStream_t s);
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
                            int *comp, u64 *best0, u64 *best1, u64 *er, long long er_cap, unsigned *hstamp,
                            cudaStream_t s);

@@ -52,7 +52,14 @@ def test_aggregate_single_process():
 def test_phase_bytes_model_positive():
     import bench
     st = dict(batch_len=10, applied=8, candidates=5, active=3, affected=20, detached=7, scanned=40, tree_cut=4,
-              jump_rounds=3, replacement=2, rank_rounds=2, mark_rounds=2, reversed=1)
+              jump_rounds=3, replacement=2, rank_rounds=2, mark_rounds=2, reversed=1, hook_rounds=2)
     for op in (0, 1):
         by = bench.phase_bytes(st, 100, op)
         assert all(v >= 0 for v in by.values()) and by["begin"] == 80
+    # the per-unit figures: 12 per affected vertex and doubling round; 12 per
+    # scanned row + 8 per entry + 8 per candidate; 24 per candidate and round
+    by = bench.phase_bytes(st, 100, 1)
+    assert by["jump"] == 12 * 20 * 3
+    assert by["scan"] == 12 * 7 + 8 * 40 + 8 * 5
+    assert by["hook"] == 24 * 5 * 2
+    assert by["reverse"] == 12 * 1 + 8 * 2
