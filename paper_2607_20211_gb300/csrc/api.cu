@@ -517,7 +517,7 @@ static drsf_status create_impl(drsf_ctx *h, const int32_t *edges, int64_t m, con
     // representatives of F by pointer jumping over all vertices
     Csr g0{h->off, h->used, h->col};
     CK(launch_jump(h->dev, nullptr, 0, n, h->ctl, h->parent, h->J0, h->J1, h->rep, rows(h), 0, h->rold, h->wgt,
-                   h->heavy, g0, h->bsum, h->jump_sync, h->act, h->xlist, h->cutlist, s));
+                   h->heavy, g0, h->jump_sync, h->act, h->xlist, h->cutlist, s));
     Ctl c{};
     CK(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -631,7 +631,7 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
         prof_end(h, PH_AFF, 1, s);
         prof_begin(h, PH_JUMP, s);
         CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->parent, h->J0, h->J1, h->rep, rows(h), 1, h->rold, h->wgt,
-                       h->heavy, g, h->bsum, h->jump_sync, h->act, h->xlist, h->cutlist, s));
+                       h->heavy, g, h->jump_sync, h->act, h->xlist, h->cutlist, s));
         prof_end(h, PH_JUMP, 1, s);
         prof_begin(h, PH_SCAN, s);
         CK(launch_scan_rows(h->dev, rows(h), ctl, g, h->rep, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
@@ -719,7 +719,7 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
     }
     prof_end(h, PH_MARK, 1, s);
     prof_begin(h, PH_REVERSE, s);
-    CK(launch_reverse(h->dev, ctl, h->act, h->pold, h->mark, h->chx, h->chy, h->parent, s));
+    CK(launch_reverse(h->dev, ctl, h->act, h->pold, h->mark, h->chx, h->chy, h->parent, euler ? 0 : 1, s));
     prof_end(h, PH_REVERSE, 1, s);
     return DRSF_OK;
 }

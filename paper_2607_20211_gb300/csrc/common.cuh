@@ -295,6 +295,38 @@ __device__ __forceinline__ void block_reserve2(u64 *ctr, const bool f[2], long l
     __syncthreads();
 }
 
+// Block-aggregated reservation of list rows together with their entry
+// ranges, from one packed counter: rows in the high 32 bits, entries in the
+// low 32 bits (the entries of all rows stay below 2^32, so the low half
+// never carries into the high half).  Row k of each thread (f[k] set, len[k]
+// entries) gets its list position pos[k] and entry offset off[k]; positions
+// and offsets follow slab order, then thread order, so the offsets are the
+// exclusive prefix sum of the lengths in list order.  One atomicAdd per
+// block; every thread of the block must call it.
+template <int K>
+__device__ __forceinline__ void block_reserve_rows(u64 *ctr, const bool f[K], const int len[K], long long pos[K],
+                                                   long long off[K]) {
+    __shared__ u64 s_rr;
+    long long pre[K], tot[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        pre[k] = block_excl_scan_ll(f[k] ? (1ll << 32) | (long long)(unsigned)len[k] : 0ll, &tot[k]);
+    long long all = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) all += tot[k];
+    if (threadIdx.x == 0) s_rr = all ? atomicAdd(ctr, (u64)all) : 0;
+    __syncthreads();
+    u64 acc = s_rr;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const u64 b = acc + (u64)pre[k];
+        pos[k] = f[k] ? (long long)(b >> 32) : -1;
+        off[k] = (long long)(b & 0xFFFFFFFFull);
+        acc += (u64)tot[k];
+    }
+    __syncthreads();
+}
+
 // 64-bit minimum over a group of lanes (mask from __match_any_sync).
 __device__ __forceinline__ u64 group_min_u64(unsigned grp, u64 k) {
     unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;

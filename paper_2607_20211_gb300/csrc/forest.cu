@@ -159,13 +159,15 @@ __device__ __noinline__ void fill_tiles(int *tile, long long st, long long d, in
 // tree finds each of them.  The piece left out is the root piece, unless a
 // detached piece has HEAVY_SWAP_MIN more vertices (a cut near the root that
 // detaches most of a tree): then the heaviest piece.  The listed rows get an
-// exclusive prefix sum of their lengths in roff (roff[ndet] = total), their
-// CSR start and their (piece, piece left out) for the load-balanced scan.
+// exclusive prefix sum of their lengths in roff (roff[ndet] = total; rows
+// and entry ranges are reserved together from one packed counter), their
+// CSR start, their (piece, piece left out) and the row of every 32-entry
+// tile for the load-balanced scan.
 // (6 blocks of BLK threads per SM: the rounds are latency-bound)
 __global__ void __launch_bounds__(BLK, 6)
     k_jump(const int *A, int use_list, long long cnt_static, Ctl *ctl, const int *par, int *J, int *J1, int *rep,
-           RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g, long long *bsum, int sync_rounds,
-           int *X, int *Y, const int *cuts) {
+           RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g, int sync_rounds, int *X, int *Y,
+           const int *cuts) {
     int *const D = rl.D;
     unsigned *const roff = rl.roff;
     if (*(volatile int *)&ctl->skip) return;
@@ -304,15 +306,16 @@ __global__ void __launch_bounds__(BLK, 6)
                     }
                 }
             }
-            long long q[JF];
-            block_reserve2(&ctl->ndet, scan, q);
+            long long q[JF], eo[JF];
+            block_reserve_rows<JF>(&ctl->ndet, scan, len, q, eo);
 #pragma unroll
             for (int k = 0; k < JF; ++k)
                 if (scan[k]) {
                     D[q[k]] = v[k];
-                    roff[q[k]] = (unsigned)len[k];
+                    roff[q[k]] = (unsigned)eo[k];
                     rl.base[q[k]] = (unsigned)g.off[v[k]];
                     rl.meta[q[k]] = make_int2(p[k], ro[k]);
+                    fill_tiles(rl.tile, eo[k], len[k], (int)q[k]);
                 }
         }
         __syncthreads();
@@ -344,6 +347,7 @@ __global__ void __launch_bounds__(BLK, 6)
     // heaviest piece per cut tree: its pieces are the root piece and one
     // piece per cut vertex, so the cut list covers them all
     const long long nc = (long long)ctl->ncut;
+    if (gtid() == 0) ctl->flag[0] = 0;   // set by the swap check below
     for (long long i = gtid(); i < nc; i += gstride()) {
         int c = cuts[i];
         int r = rold[c];
@@ -363,8 +367,6 @@ __global__ void __launch_bounds__(BLK, 6)
     if (!grid_barrier(ctl, &ctl->bar[0])) return;
     // the provisional list left out each tree's root piece; where another
     // piece is heavier, rebuild the list with the exact rule (rare)
-    if (gtid() == 0) ctl->flag[0] = 0;
-    if (!grid_barrier(ctl, &ctl->bar[0])) return;
     {
         bool swap = false;
         for (long long i = gtid(); i < nc; i += gstride()) {
@@ -380,82 +382,37 @@ __global__ void __launch_bounds__(BLK, 6)
         if (!grid_barrier(ctl, &ctl->bar[0])) return;
         for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += gstride()) {
             long long i = base + threadIdx.x;
-            bool scan = false;
-            int v = 0, hp = 0, pv = 0;
-            long long len = 0;
+            bool scan[1] = {false};
+            int v = 0, hp = 0, pv = 0, len[1] = {0};
             if (i < cnt) {
                 v = A[i];
                 hp = (int)(unsigned)LD(heavy[rold[v]]);
-                long long cap = g.off[v + 1] - g.off[v];
-                long long used = g.used[v];
-                len = used < cap ? used : cap;
+                int cap = (int)(g.off[v + 1] - g.off[v]);
+                int used = g.used[v];
+                len[0] = used < cap ? used : cap;
                 pv = LD(rep[v]);
-                scan = pv != hp && len > 0;
+                scan[0] = pv != hp && len[0] > 0;
             }
-            long long q = block_append(&ctl->ndet, scan);
-            if (scan) {
-                D[q] = v;
-                roff[q] = (unsigned)len;
-                rl.base[q] = (unsigned)g.off[v];
-                rl.meta[q] = make_int2(pv, hp);
+            long long q[1], eo[1];
+            block_reserve_rows<1>(&ctl->ndet, scan, len, q, eo);
+            if (scan[0]) {
+                D[q[0]] = v;
+                roff[q[0]] = (unsigned)eo[0];
+                rl.base[q[0]] = (unsigned)g.off[v];
+                rl.meta[q[0]] = make_int2(pv, hp);
+                fill_tiles(rl.tile, eo[0], len[0], (int)q[0]);
             }
         }
+        if (!grid_barrier(ctl, &ctl->bar[0])) return;
     }
-    if (!grid_barrier(ctl, &ctl->bar[0])) return;
-    // exclusive scan of roff[0..nd) in place: chunk sums, scan of the sums,
-    // chunk rescans
-    const long long nd = (long long)*(volatile u64 *)&ctl->ndet;
-    const long long chunk = (nd + gridDim.x - 1) / gridDim.x;
-    const long long lo = (long long)blockIdx.x * chunk, hi = lo + chunk < nd ? lo + chunk : nd;
-    {
-        long long sacc = 0;
-        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) sacc += LD(roff[i]);
-        long long tot;
-        block_excl_scan_ll(sacc, &tot);
-        if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
-    }
-    if (!grid_barrier(ctl, &ctl->bar[0])) return;
-    if (blockIdx.x == 0) {
-        long long nbk = gridDim.x;
-        long long per = (nbk + blockDim.x - 1) / blockDim.x;
-        long long l0 = threadIdx.x * per, l1 = l0 + per < nbk ? l0 + per : nbk;
-        long long sacc = 0;
-        for (long long i = l0; i < l1; ++i) sacc += LD(bsum[i]);
-        long long tot;
-        long long pre = block_excl_scan_ll(sacc, &tot);
-        for (long long i = l0; i < l1; ++i) {
-            long long t = LD(bsum[i]);
-            bsum[i] = pre;
-            pre += t;
-        }
-        if (threadIdx.x == 0) roff[nd] = (unsigned)tot;
-    }
-    if (!grid_barrier(ctl, &ctl->bar[0])) return;
-    {
-        long long carry = LD(bsum[blockIdx.x]);
-        for (long long t0 = lo; t0 < hi; t0 += blockDim.x) {
-            long long i = t0 + threadIdx.x;
-            long long d = i < hi ? LD(roff[i]) : 0;
-            long long tot;
-            long long pre = block_excl_scan_ll(d, &tot);
-            if (i < hi) {
-                const long long st = carry + pre;
-                roff[i] = (unsigned)st;
-                fill_tiles(rl.tile, st, d, (int)i);
-            }
-            carry += tot;
-        }
+    // the packed row counter becomes the row count; roff[nd] = all entries
+    if (gtid() == 0) {
+        const u64 pk = *(volatile u64 *)&ctl->ndet;
+        ctl->ndet = pk >> 32;
+        roff[pk >> 32] = (unsigned)pk;
     }
 }
 
-// Replacement edges by hook-and-compress over the trees of F^ (pieces).
-// Each round: every component takes the minimum key among its incident
-// candidates (64-bit atomicMin); a component whose minimum edge leads to
-// another component hooks onto it (a mutual choice hooks the larger id under
-// the smaller); each hooking edge joins E_r.  Candidates inside one
-// component are dropped, the rest are compacted for the next round.  With
-// distinct keys this is Boruvka's algorithm: E_r is the unique minimum
-// spanning forest of the piece multigraph, |E_r| = k - l.
 // Per-block table of hot indices for 64-bit minimum updates: lanes of a
 // warp with the same index combine first; an index held by two or more
 // lanes of a warp (one piece, such as the giant one, can be an endpoint of
@@ -682,16 +639,22 @@ __global__ void __launch_bounds__(ORIENT_THREADS) k_orient(Ctl *ctl, OrientArgs 
     // (eroot), so no phase re-walks rep / pidx / the hook forest.
     // phase 1: dense ids for the pieces touched by E_r
     if (gtid() == 0) ctl->ncore = 0;
-    for (long long j = gtid(); j < 2 * ner; j += gstride()) {
-        u64 k = a.er[j >> 1];
-        int p = a.rep[(j & 1) ? khi(k) : klo(k)];
-        a.ep[j] = p;
-        // one lane per piece among the warp's lanes claims it (a piece such
-        // as the giant one is an endpoint of most of the batch's edges)
-        unsigned grp = __match_any_sync(__activemask(), p);
-        bool lead = (int)(threadIdx.x & 31) == __ffs(grp) - 1;
-        bool first = lead && __ldcg(&a.pstamp[p]) != ep && atomicExch(&a.pstamp[p], ep) != ep;
-        long long id = agg_append(&ctl->npc, first);
+    // (block-uniform loop: the dense ids are reserved once per block)
+    for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < 2 * ner; b0 += gstride()) {
+        const long long j = b0 + threadIdx.x;
+        bool first = false;
+        int p = 0;
+        if (j < 2 * ner) {
+            u64 k = a.er[j >> 1];
+            p = a.rep[(j & 1) ? khi(k) : klo(k)];
+            a.ep[j] = p;
+            // one lane per piece among the warp's lanes claims it (a piece
+            // such as the giant one is an endpoint of most of the edges)
+            unsigned grp = __match_any_sync(__activemask(), p);
+            bool lead = (int)(threadIdx.x & 31) == __ffs(grp) - 1;
+            first = lead && __ldcg(&a.pstamp[p]) != ep && atomicExch(&a.pstamp[p], ep) != ep;
+        }
+        long long id = block_append(&ctl->npc, first);
         if (first) {
             a.pidx[p] = (int)id;
             a.plist[id] = p;
@@ -1043,9 +1006,10 @@ __global__ void k_mark(Ctl *ctl, const int *act, int *J0, int *J1, unsigned char
 // no thread reads a pointer another thread rewrites); then parent[x] = y for
 // every oriented replacement edge x -> y.
 __global__ void k_reverse(Ctl *ctl, const int *act, const int *pold, const unsigned char *mark, const int *chx,
-                          const int *chy, int *parent) {
+                          const int *chy, int *parent, int walked) {
     if (*(volatile int *)&ctl->skip) return;
     long long na = (long long)ctl->nact, ner = (long long)ctl->ner;
+    if (walked && na == 0) return;   // every piece was reversed and attached by its walk
     long long c = 0;
     GS_LOOP(i, na) {
         int v = act[i];
@@ -1118,11 +1082,11 @@ cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsign
 }
 cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, const int *par,
                         int *J, int *J1, int *rep, RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy,
-                        Csr g, long long *bsum, int sync_rounds, int *X, int *Y, const int *cuts, cudaStream_t s) {
-    void *args[] = {(void *)&A, (void *)&use_list, (void *)&cnt_static, (void *)&ctl, (void *)&par, (void *)&J,
-                    (void *)&J1, (void *)&rep, (void *)&rl, (void *)&mode, (void *)&rold, (void *)&w,
-                    (void *)&heavy, (void *)&g, (void *)&bsum, (void *)&sync_rounds, (void *)&X, (void *)&Y,
-                    (void *)&cuts};
+                        Csr g, int sync_rounds, int *X, int *Y, const int *cuts, cudaStream_t s) {
+    void *args[] = {(void *)&A,    (void *)&use_list, (void *)&cnt_static, (void *)&ctl,   (void *)&par,
+                    (void *)&J,    (void *)&J1,       (void *)&rep,        (void *)&rl,    (void *)&mode,
+                    (void *)&rold, (void *)&w,        (void *)&heavy,      (void *)&g,     (void *)&sync_rounds,
+                    (void *)&X,    (void *)&Y,        (void *)&cuts};
     return cudaLaunchCooperativeKernel((const void *)k_jump, d.coop_jump, BLK, args, 0, s);
 }
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
@@ -1158,8 +1122,8 @@ cudaError_t launch_mark(const Dev &d, Ctl *ctl, const int *act, int *J0, int *J1
     return cudaLaunchCooperativeKernel((const void *)k_mark, d.coop_mark, BLK, args, 0, s);
 }
 cudaError_t launch_reverse(const Dev &d, Ctl *ctl, const int *act, const int *pold, const unsigned char *mark,
-                           const int *chx, const int *chy, int *parent, cudaStream_t s) {
-    k_reverse<<<d.grid, BLK, 0, s>>>(ctl, act, pold, mark, chx, chy, parent);
+                           const int *chx, const int *chy, int *parent, int walked, cudaStream_t s) {
+    k_reverse<<<d.grid, BLK, 0, s>>>(ctl, act, pold, mark, chx, chy, parent, walked);
     return cudaGetLastError();
 }
 cudaError_t launch_labels(int n, const int *rep, int *tmp, int *out, cudaStream_t s) {

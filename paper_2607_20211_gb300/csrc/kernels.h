@@ -71,7 +71,7 @@ cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsign
                                unsigned *w, u64 *heavy, Ctl *ctl, cudaStream_t s);
 cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, const int *par,
                         int *J, int *J1, int *rep, RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy,
-                        Csr g, long long *bsum, int sync_rounds, int *X, int *Y, const int *cuts, cudaStream_t s);
+                        Csr g, int sync_rounds, int *X, int *Y, const int *cuts, cudaStream_t s);
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
                            int *comp, u64 *best0, u64 *best1, u64 *er, long long er_cap, unsigned *hstamp,
                            cudaStream_t s);
@@ -101,7 +101,7 @@ cudaError_t launch_active(const Dev &d, const int *L, int use_list, long long cn
 cudaError_t launch_mark(const Dev &d, Ctl *ctl, const int *act, int *J0, int *J1, unsigned char *mark,
                         const int *parent, cudaStream_t s);
 cudaError_t launch_reverse(const Dev &d, Ctl *ctl, const int *act, const int *pold, const unsigned char *mark,
-                           const int *chx, const int *chy, int *parent, cudaStream_t s);
+                           const int *chx, const int *chy, int *parent, int walked, cudaStream_t s);
 cudaError_t launch_labels(int n, const int *rep, int *tmp, int *out, cudaStream_t s);
 
 unsigned coop_blocks_jump(int nsm);
