@@ -401,6 +401,19 @@ __device__ __forceinline__ int find_root(int *comp, int x, Ctl *ctl) {
     return x;
 }
 
+// Root of x in the hook forest without writes (for short chains read by
+// many threads at once: no stores to shared entries).  Bounded; a cycle
+// latches ERR_ROUNDS.
+__device__ __forceinline__ int find_root_ro(const int *comp, int x, Ctl *ctl) {
+    for (int it = 0; it < (1 << 24); ++it) {
+        int p = __ldcg(&comp[x]);
+        if (p == x) return x;
+        x = p;
+    }
+    atomicOr(&ctl->err, ERR_ROUNDS);
+    return x;
+}
+
 // Loads of data that other blocks wrote earlier in the same cooperative
 // launch go to L2 (the SM's L1 may hold a stale line).
 #define LD(x) __ldcg(&(x))

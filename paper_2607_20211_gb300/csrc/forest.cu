@@ -535,8 +535,8 @@ __global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int 
         for (long long i = gtid(); i < c; i += gstride()) {
             int a = LD(ca[i]), b = LD(cb[i]);
             if (r > 0) {   // every endpoint is its own root in round 0
-                a = find_root(comp, a, ctl);
-                b = find_root(comp, b, ctl);
+                a = find_root_ro(comp, a, ctl);
+                b = find_root_ro(comp, b, ctl);
                 ca[i] = a;
                 cb[i] = b;
             }

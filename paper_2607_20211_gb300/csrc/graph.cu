@@ -309,11 +309,15 @@ __global__ void k_del_claim(const int *batch, long long len, Index ix, Csr g, u6
     long long loops = 0, drops = 0, wins = 0;
     for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < len; b0 += (long long)gridDim.x * blockDim.x) {
         const long long i = b0 + threadIdx.x;
-        int c = -1;
+        int c = -1, rc = -1;
         if (i < len) {
             int u = batch[2 * i], v = batch[2 * i + 1];
             bool won = false;
             if (u != v) {
+                // loaded up front, beside the index probe: parent[u] changes in
+                // this kernel only by the cut of the edge {u, parent[u]}, which
+                // only the thread deleting that edge makes
+                const int par_u = parent[u], par_v = parent[v], rep_u = rep[u], rep_v = rep[v];
                 u64 key = ekey((uint32_t)u, (uint32_t)v);
                 long long s = index_find(ix, key);
                 if (s >= 0) won = atomicCAS(&ix.key[s], key, TOMB_KEY) == key;
@@ -325,8 +329,13 @@ __global__ void k_del_claim(const int *batch, long long len, Index ix, Csr g, u6
                         g.col[pu] = -1;
                         g.col[pv] = -1;
                     }
-                    if (parent[u] == v) c = u;
-                    else if (parent[v] == u) c = v;
+                    if (par_u == v) {
+                        c = u;
+                        rc = rep_u;
+                    } else if (par_v == u) {
+                        c = v;
+                        rc = rep_v;
+                    }
                     if (c >= 0) {
                         parent[c] = c;
                         cut_ep[c] = ep;
@@ -342,7 +351,7 @@ __global__ void k_del_claim(const int *batch, long long len, Index ix, Csr g, u6
         {
             // stamp the cut trees' old roots; lanes cutting the same tree
             // write once (most cuts can fall in one giant tree)
-            int r = c >= 0 ? rep[c] : -1;
+            int r = rc;
             unsigned m = __ballot_sync(0xffffffffu, c >= 0);
             if (c >= 0) {
                 unsigned grp = __match_any_sync(m, r);
