@@ -182,7 +182,8 @@ def phase_bytes(st: dict, n: int, op: int) -> dict:
     each data item the method must touch, counted once per pass, uncached
     (per-unit figures: a0 24 per batch edge, a1 insert 16 + two 32-byte index
     probes per applied edge, a1 delete two probes + an 8-byte tombstone, a2 4
-    per batch edge for the cut and 12 per affected vertex and doubling round,
+    per batch edge for the cut and 12 per doubling step taken (at most 12 per
+    affected vertex and doubling round),
     a3 12 per scanned row + 8 per scanned entry + 8 per candidate and 24 per
     candidate and hooking round, a4 64 r log2 r, a5 13 per active vertex and
     marking round + 12 per reversed vertex, a6 8 per vertex of the pass)."""
@@ -196,7 +197,9 @@ def phase_bytes(st: dict, n: int, op: int) -> dict:
         aff = st["affected"]
         out["del_claim"] = 16 * b + 72 * a + 4 * b
         out["affected"] = 8 * n
-        out["jump"] = 12 * aff * max(st["jump_rounds"], 1)
+        # each doubling step taken (a visit: read J, gather J[J], write) counts
+        # 12 bytes; the steps taken stay below affected x doubling rounds
+        out["jump"] = 12 * st.get("jump_visits", aff * max(st["jump_rounds"], 1))
         out["scan"] = 12 * st["detached"] + 8 * st["scanned"] + 8 * st["candidates"]
         out["active"] = 8 * aff
     c, ner = st["candidates"], st["replacement"]

@@ -114,11 +114,14 @@ typedef struct {
                               DRSF_EULER_REVERSAL) */
     int64_t reversed;      /* vertices whose parent pointer was reversed */
     int64_t mark_rounds;   /* pointer-doubling rounds of the path reversal */
-    int64_t jump_rounds;   /* pointer-jumping rounds for representatives */
+    int64_t jump_rounds;   /* pointer-jumping steps for representatives: the
+                              most steps any warp took (asynchronous
+                              doubling, the default), or the rounds of the
+                              synchronous variant */
     int64_t edges;         /* |E(G')| after the batch */
     int64_t overflow;      /* edges held outside their CSR row (slack exhausted) */
     int64_t rebuilds;      /* CSR / index rebuilds so far */
-    int64_t jump_visits;   /* vertex visits summed over the pointer-jumping rounds */
+    int64_t jump_visits;   /* vertex visits summed over the pointer-jumping steps */
 } drsf_batch_stats;
 
 /* Allocator hooks.  alloc(bytes, stream, ctx) returns device memory or NULL;

@@ -32,7 +32,7 @@ struct drsf_ctx {
     void *alloc_ctx = nullptr;
     std::vector<Buf> bufs;
     bool poisoned = false;
-    int jump_sync = 1;   // root search: 1 synchronous doubling rounds, 0 in-place path halving
+    int jump_sync = 2;   // root search: 2 asynchronous doubling, 1 synchronous rounds, 0 path halving
     int pending_einval = 0;
 
     Ctl *ctl = nullptr;
@@ -517,7 +517,7 @@ static drsf_status create_impl(drsf_ctx *h, const int32_t *edges, int64_t m, con
     // representatives of F by pointer jumping over all vertices
     Csr g0{h->off, h->used, h->col};
     CK(launch_jump(h->dev, nullptr, 0, n, h->ctl, h->parent, h->J0, h->J1, h->rep, rows(h), 0, h->rold, h->wgt,
-                   h->heavy, g0, h->jump_sync, h->act, h->xlist, h->cutlist, s));
+                   h->heavy, g0, h->jump_sync == 2 ? 1 : h->jump_sync, h->act, h->xlist, h->cutlist, s));
     Ctl c{};
     CK(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -583,9 +583,11 @@ drsf_status drsf_create(int32_t n, const int32_t *edges, int64_t m, const int32_
     h->dev.coop_bfs = coop_blocks_bfs(nsm);
     h->dev.grid_scan = scan_grid(nsm);
     h->dev.coop_et = coop_blocks_et(nsm);
-    // DRSF_JUMP=halving selects the in-place path-halving root search
+    // root search of a delete batch: barrier-free doubling over per-warp
+    // slices by default; DRSF_JUMP=sync selects synchronous doubling rounds,
+    // DRSF_JUMP=halving the in-place path-halving walks
     const char *jm = getenv("DRSF_JUMP");
-    h->jump_sync = (jm && strcmp(jm, "halving") == 0) ? 0 : 1;
+    h->jump_sync = jm && strcmp(jm, "halving") == 0 ? 0 : (jm && strcmp(jm, "sync") == 0 ? 1 : 2);
     drsf_status st = create_impl(h, edges, m, parent, s);
     if (st != DRSF_OK) {
         destroy_all(h);
@@ -627,9 +629,11 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
                             h->cutlist, h->wgt, s));
         prof_end(h, PH_DEL_CLAIM, len > 0 ? 1 : 0, s);
         prof_begin(h, PH_AFF, s);
-        CK(launch_aff_collect(h->dev, h->n, h->rep, h->aff_ep, h->A, h->rold, h->wgt, h->heavy, ctl, s));
+        CK(launch_aff_collect(h->dev, h->n, h->rep, h->aff_ep, h->A, h->rold, h->wgt, h->heavy, ctl, h->parent,
+                              h->jump_sync == 2 ? h->J0 : nullptr, s));
         prof_end(h, PH_AFF, 1, s);
         prof_begin(h, PH_JUMP, s);
+        if (h->jump_sync == 2) CK(launch_jump_async(h->dev, h->A, ctl, h->J0, h->act, h->xlist, s));
         CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->parent, h->J0, h->J1, h->rep, rows(h), 1, h->rold, h->wgt,
                        h->heavy, g, h->jump_sync, h->act, h->xlist, h->cutlist, s));
         prof_end(h, PH_JUMP, 1, s);

@@ -83,7 +83,7 @@ __global__ void k_begin(Ctl *ctl, int op, long long len) {
 // of rep, IPT gathers in flight) and the block reserves its list slots with
 // one atomic; the list stays in vertex order.
 __global__ void k_aff_collect(int n, const int *rep, const unsigned *aff_ep, int *A, int *rold, unsigned *w,
-                              u64 *heavy, Ctl *ctl) {
+                              u64 *heavy, Ctl *ctl, const int *par, int *J) {
     if (*(volatile int *)&ctl->skip) return;
     unsigned ep = ctl->epoch;
     const long long step = (long long)gridDim.x * blockDim.x * IPT;
@@ -105,6 +105,7 @@ __global__ void k_aff_collect(int n, const int *rep, const unsigned *aff_ep, int
             const int v = (int)(v0 + k);
             A[p++] = v;
             rold[v] = r[k];
+            if (J) J[v] = par[v];   // seed of the asynchronous doubling
             if (r[k] == v) {   // the old root: piece-weight and heaviest-piece slots
                 w[v] = 0;
                 heavy[v] = 0;
@@ -152,6 +153,81 @@ __device__ __noinline__ void fill_tiles(int *tile, long long st, long long d, in
     for (long long T = (st + 31) >> 5; T <= (st + d - 1) >> 5; ++T) tile[T] = row;
 }
 
+// Representatives by asynchronous pointer doubling in place (delete batches
+// with DRSF_JUMP=async): no grid barrier between steps.  J holds a copy of
+// the cut forest for the listed vertices; afterwards J[v] is the complemented
+// root of every listed vertex, and k_jump<2> carries on from there.
+__global__ void __launch_bounds__(BLK, 6) k_jump_async(const int *A, Ctl *ctl, int *J, int *X, int *Y) {
+    if (*(volatile int *)&ctl->skip) return;
+    const long long cnt = (long long)ctl->naff;
+    // asynchronous doubling in place (one buffer, no grid barrier
+    // between steps): each warp owns a slice of the list and repeats
+    // J[v] <- J[J[v]] over its open vertices until none is left.  A
+    // pointer only ever moves to an ancestor, whatever mix of old and
+    // new values a step reads, so every step moves an open vertex up
+    // at least one level and the result is the same roots.
+    // (list positions are below 2^31: at most n entries)
+    const int lane = threadIdx.x & 31;
+    const int nwarp = (int)(gstride() >> 5);
+    const int slice = (int)((cnt + nwarp - 1) / nwarp);
+    const int wlo = (int)(gtid() >> 5) * slice;
+    int wlen = wlo < cnt ? (int)(wlo + slice < cnt ? slice : cnt - wlo) : 0;
+    const int *in = A + wlo;
+    int *out = X + wlo, *spare = Y + wlo;
+    int it = 0;
+    long long vis = 0;
+    while (wlen > 0) {
+        if (it >= MAX_ROUNDS * 64) {
+            if (lane == 0) atomicOr(&ctl->err, ERR_ROUNDS);
+            return;
+        }
+        vis += wlen;
+        int nopen = 0;
+        for (int b0 = 0; b0 < wlen; b0 += 32 * JU) {
+            int v[JU], w0[JU], w2[JU];
+            bool ok[JU], open[JU];
+#pragma unroll
+            for (int k = 0; k < JU; ++k) {
+                const int i = b0 + k * 32 + lane;
+                ok[k] = i < wlen;
+                v[k] = ok[k] ? in[i] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < JU; ++k) w0[k] = ok[k] ? LD(J[v[k]]) : -1;
+#pragma unroll
+            for (int k = 0; k < JU; ++k) w2[k] = (ok[k] && w0[k] >= 0) ? LD(J[w0[k]]) : 0;
+#pragma unroll
+            for (int k = 0; k < JU; ++k) {
+                open[k] = false;
+                if (!ok[k]) continue;
+                int nv;
+                if (w0[k] < 0) nv = w0[k];
+                else if (w2[k] < 0) nv = w2[k];
+                else if (w2[k] == w0[k]) nv = ~w0[k];
+                else {
+                    nv = w2[k];
+                    open[k] = true;
+                }
+                J[v[k]] = nv;
+            }
+#pragma unroll
+            for (int k = 0; k < JU; ++k) {
+                const unsigned m = __ballot_sync(0xffffffffu, open[k]);
+                if (open[k]) out[nopen + __popc(m & ((1u << lane) - 1u))] = v[k];
+                nopen += __popc(m);
+            }
+        }
+        wlen = nopen;
+        in = out;
+        int *t = out; out = spare; spare = t;
+        ++it;
+    }
+    if (lane == 0 && vis) {
+        atomicAdd((u64 *)&ctl->jump_visits, (u64)vis);
+        atomicMax((unsigned long long *)&ctl->jump_rounds, (unsigned long long)it);
+    }
+}
+
 // Representatives (Algorithm 1, parallel pointer jumping) of the listed
 // vertices: rep[v] = root of v in F^ (J starts as a copy of parent).
 // Delete mode (1) then chooses the rows to scan for cross edges: every cross
@@ -164,15 +240,15 @@ __device__ __noinline__ void fill_tiles(int *tile, long long st, long long d, in
 // CSR start, their (piece, piece left out) and the row of every 32-entry
 // tile for the load-balanced scan.
 // (6 blocks of BLK threads per SM: the rounds are latency-bound)
+template <int sync_rounds>
 __global__ void __launch_bounds__(BLK, 6)
     k_jump(const int *A, int use_list, long long cnt_static, Ctl *ctl, const int *par, int *J, int *J1, int *rep,
-           RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g, int sync_rounds, int *X, int *Y,
-           const int *cuts) {
+           RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy, Csr g, int *X, int *Y, const int *cuts) {
     int *const D = rl.D;
     unsigned *const roff = rl.roff;
     if (*(volatile int *)&ctl->skip) return;
     long long cnt = use_list ? (long long)ctl->naff : cnt_static;
-    if (sync_rounds) {
+    if constexpr (sync_rounds != 0) {
         // synchronous doubling J <- J o J (ping-pong).  A pointer that has
         // reached a root is stored complemented (negative): a converged
         // vertex skips the gather, and the loop ends in the first round in
@@ -185,6 +261,9 @@ __global__ void __launch_bounds__(BLK, 6)
         // (par); its converged vertices still write both buffers.
         int *Jc = J, *Jn = J1;
         int r = 0;
+        if constexpr (sync_rounds == 2) {
+            // the roots were found by k_jump_async (complemented in J)
+        } else {
         if (gtid() == 0) {
             ctl->cnt[0] = (u64)cnt;
             ctl->cnt[1] = 0;
@@ -245,6 +324,7 @@ __global__ void __launch_bounds__(BLK, 6)
             int *t = Jc; Jc = Jn; Jn = t;
         }
         if (gtid() == 0) ctl->jump_rounds = r;
+        }
         if (mode == 0) {
             for (long long i = gtid(); i < cnt; i += gstride()) {
                 int v = use_list ? A[i] : (int)i;
@@ -1056,7 +1136,12 @@ static unsigned coop_blocks(const void *fn, int nsm, int cap_per_sm) {
     if (per > cap_per_sm) per = cap_per_sm;
     return (unsigned)(per * nsm);
 }
-unsigned coop_blocks_jump(int nsm) { return coop_blocks((const void *)k_jump, nsm, 8); }
+unsigned coop_blocks_jump(int nsm) {
+    // the three root-search variants share one launch bound; take the least
+    unsigned a = coop_blocks((const void *)k_jump<0>, nsm, 8), b = coop_blocks((const void *)k_jump<1>, nsm, 8),
+             c = coop_blocks((const void *)k_jump<2>, nsm, 8);
+    return a < b ? (a < c ? a : c) : (b < c ? b : c);
+}
 unsigned coop_blocks_hook(int nsm) { return coop_blocks((const void *)k_boruvka, nsm, 4); }
 unsigned coop_blocks_orient(int nsm) {
     cudaFuncSetAttribute((const void *)k_orient, cudaFuncAttributeMaxDynamicSharedMemorySize, ORIENT_SMEM_BYTES);
@@ -1075,19 +1160,25 @@ cudaError_t launch_begin(Ctl *ctl, int op, long long len, cudaStream_t s) {
     return cudaGetLastError();
 }
 cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, int *A, int *rold,
-                               unsigned *w, u64 *heavy, Ctl *ctl, cudaStream_t s) {
-    k_aff_collect<<<gsz((n + IPT - 1) / IPT), BLK, 0, s>>>(n, rep, aff_ep, A, rold, w, heavy, ctl);
+                               unsigned *w, u64 *heavy, Ctl *ctl, const int *par, int *J, cudaStream_t s) {
+    k_aff_collect<<<gsz((n + IPT - 1) / IPT), BLK, 0, s>>>(n, rep, aff_ep, A, rold, w, heavy, ctl, par, J);
     (void)d;
+    return cudaGetLastError();
+}
+cudaError_t launch_jump_async(const Dev &d, const int *A, Ctl *ctl, int *J, int *X, int *Y, cudaStream_t s) {
+    k_jump_async<<<d.coop_jump, BLK, 0, s>>>(A, ctl, J, X, Y);
     return cudaGetLastError();
 }
 cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, const int *par,
                         int *J, int *J1, int *rep, RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy,
                         Csr g, int sync_rounds, int *X, int *Y, const int *cuts, cudaStream_t s) {
-    void *args[] = {(void *)&A,    (void *)&use_list, (void *)&cnt_static, (void *)&ctl,   (void *)&par,
-                    (void *)&J,    (void *)&J1,       (void *)&rep,        (void *)&rl,    (void *)&mode,
-                    (void *)&rold, (void *)&w,        (void *)&heavy,      (void *)&g,     (void *)&sync_rounds,
-                    (void *)&X,    (void *)&Y,        (void *)&cuts};
-    return cudaLaunchCooperativeKernel((const void *)k_jump, d.coop_jump, BLK, args, 0, s);
+    void *args[] = {(void *)&A,    (void *)&use_list, (void *)&cnt_static, (void *)&ctl, (void *)&par,
+                    (void *)&J,    (void *)&J1,       (void *)&rep,        (void *)&rl,  (void *)&mode,
+                    (void *)&rold, (void *)&w,        (void *)&heavy,      (void *)&g,   (void *)&X,
+                    (void *)&Y,    (void *)&cuts};
+    const void *fn = sync_rounds == 2 ? (const void *)k_jump<2>
+                                      : (sync_rounds ? (const void *)k_jump<1> : (const void *)k_jump<0>);
+    return cudaLaunchCooperativeKernel(fn, d.coop_jump, BLK, args, 0, s);
 }
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
                            int *comp, u64 *best0, u64 *best1, u64 *er, long long er_cap, unsigned *hstamp,

@@ -68,7 +68,8 @@ cudaError_t launch_check_cross(const int *pairs, long long m, const int *rep, in
 // forest.cu ------------------------------------------------------------
 cudaError_t launch_begin(Ctl *ctl, int op, long long len, cudaStream_t s);
 cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, int *A, int *rold,
-                               unsigned *w, u64 *heavy, Ctl *ctl, cudaStream_t s);
+                               unsigned *w, u64 *heavy, Ctl *ctl, const int *par, int *J, cudaStream_t s);
+cudaError_t launch_jump_async(const Dev &d, const int *A, Ctl *ctl, int *J, int *X, int *Y, cudaStream_t s);
 cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, const int *par,
                         int *J, int *J1, int *rep, RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy,
                         Csr g, int sync_rounds, int *X, int *Y, const int *cuts, cudaStream_t s);

@@ -59,7 +59,9 @@ def test_phase_bytes_model_positive():
     # the per-unit figures: 12 per affected vertex and doubling round; 12 per
     # scanned row + 8 per entry + 8 per candidate; 24 per candidate and round
     by = bench.phase_bytes(st, 100, 1)
-    assert by["jump"] == 12 * 20 * 3
+    assert by["jump"] == 12 * 20 * 3   # no visit count: affected x rounds
+    st2 = dict(st, jump_visits=45)
+    assert bench.phase_bytes(st2, 100, 1)["jump"] == 12 * 45
     assert by["scan"] == 12 * 7 + 8 * 40 + 8 * 5
     assert by["hook"] == 24 * 5 * 2
     assert by["reverse"] == 12 * 1 + 8 * 2
