@@ -398,9 +398,12 @@ __global__ void k_scan_lb(RowList rl, Ctl *ctl, Csr g, const int *rep, PairTable
     if (warp == 0 && lane == 0) atomicAdd((u64 *)&ctl->scanned, (u64)E);
     const unsigned per = (NT + nw - 1) / nw;
     const unsigned t_lo = warp * per, t_hi = t_lo + per < NT ? t_lo + per : NT;
-    // the pair-table slot this lane used last (a hub row repeats one piece
-    // pair over many tiles: no probe for it)
-    u64 cpair = EMPTY_KEY, cslot = 0;
+    // the pair this lane updated last, its table slot and the minimum key
+    // seen for it since: a hub row repeats one piece pair over many tiles,
+    // so its minimum is kept in a register and written to the table once
+    // when the pair changes (no probe, and no stream of atomics on one
+    // slot from every tile of the row)
+    u64 cpair = EMPTY_KEY, cslot = 0, cmin = EMPTY_KEY;
     for (unsigned T = t_lo; T < t_hi; ++T) {
         const unsigned t0 = T << 5;
         // window: rows r0 .. r0+31 from the tile's first row
@@ -445,13 +448,14 @@ __global__ void k_scan_lb(RowList rl, Ctl *ctl, Csr g, const int *rep, PairTable
                 const u64 pair = ru < rx ? ((u64)(unsigned)ru << 32) | (unsigned)rx
                                          : ((u64)(unsigned)rx << 32) | (unsigned)ru;
                 if (pair == cpair) {
-                    atomicMin(&pt.mk[cslot], key);
+                    cmin = key < cmin ? key : cmin;
                 } else {
                     const long long sl = pair_slot(pt.pk, pt.mask, pair);
                     if (sl >= 0) {
-                        atomicMin(&pt.mk[sl], key);
+                        if (cpair != EMPTY_KEY) atomicMin(&pt.mk[cslot], cmin);
                         cpair = pair;
                         cslot = (u64)sl;
+                        cmin = key;
                     } else {
                         raw = true;
                     }
@@ -469,6 +473,7 @@ __global__ void k_scan_lb(RowList rl, Ctl *ctl, Csr g, const int *rep, PairTable
             }
         }
     }
+    if (cpair != EMPTY_KEY) atomicMin(&pt.mk[cslot], cmin);
 }
 
 // Delete, cross-edge scan of the overflow list (edges outside their rows),
