@@ -43,7 +43,8 @@ struct Ctl {
     int skip;               // current batch rejected (ERR_BATCH_ID seen)
     unsigned epoch;         // batch counter; epoch stamps compare against it
     int op;
-    u64 bar[6];             // grid-barrier counters: jump, hook, orient, mark, bfs, spare
+    u64 bar[6];             // grid-barrier counters: jump, hook, orient, mark, bfs, Euler marks
+                            // (reset at each batch's start and before each static BFS)
     int flag[3];            // per-round "another round needed" flags
     u64 cnt[3];             // per-round list sizes (hook-and-compress)
     u64 nb;                 // normalised batch edges (new / deleted keys)

@@ -75,6 +75,11 @@ __global__ void k_begin(Ctl *ctl, int op, long long len) {
         ctl->flag[i] = 0;
         ctl->cnt[i] = 0;
     }
+    // each barrier counter serves one cooperative launch per batch; its
+    // targets are multiples of that launch's grid size, so it restarts at 0
+    // (launches of different grid sizes, or a wait that timed out, leave it
+    // at any value)
+    for (int i = 0; i < 6; ++i) ctl->bar[i] = 0;
 }
 
 // Delete: list the vertices of every tree that lost a tree edge (its old

@@ -153,6 +153,8 @@ cudaError_t launch_static_forest(const Dev &d, int n, Csr g, const u64 *ovf, Ctl
     unsigned gn = grid_for(n, BLK, 152u * 16u);
     cudaError_t e = cudaMemsetAsync(ctl->cnt, 0, sizeof(ctl->cnt), s);
     if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(&ctl->bar[4], 0, sizeof(u64), s);   // BFS barrier counter
+    if (e != cudaSuccess) return e;
     k_cc_init<<<gn, BLK, 0, s>>>(n, lab);
     k_cc_hook<<<d.grid, BLK, 0, s>>>(n, g, ovf, ctl, lab);
     k_cc_roots<<<gn, BLK, 0, s>>>(n, lab, comp, parent, f0, &ctl->cnt[0]);
