@@ -1141,6 +1141,12 @@ static unsigned coop_blocks(const void *fn, int nsm, int cap_per_sm) {
     if (per > cap_per_sm) per = cap_per_sm;
     return (unsigned)(per * nsm);
 }
+// The vertex passes (k_aff_collect, k_active) loop over their range with
+// the blocks that are resident at once: no partial last wave.
+unsigned grid_vertex_pass(int nsm) {
+    unsigned a = coop_blocks((const void *)k_aff_collect, nsm, 8), b = coop_blocks((const void *)k_active, nsm, 8);
+    return a < b ? a : b;
+}
 unsigned coop_blocks_jump(int nsm) {
     // the three root-search variants share one launch bound; take the least
     unsigned a = coop_blocks((const void *)k_jump<0>, nsm, 8), b = coop_blocks((const void *)k_jump<1>, nsm, 8),
@@ -1166,7 +1172,7 @@ cudaError_t launch_begin(Ctl *ctl, int op, long long len, cudaStream_t s) {
 }
 cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, int *A, int *rold,
                                unsigned *w, u64 *heavy, Ctl *ctl, const int *par, int *J, cudaStream_t s) {
-    k_aff_collect<<<gsz((n + IPT - 1) / IPT), BLK, 0, s>>>(n, rep, aff_ep, A, rold, w, heavy, ctl, par, J);
+    k_aff_collect<<<d.grid_pass, BLK, 0, s>>>(n, rep, aff_ep, A, rold, w, heavy, ctl, par, J);
     (void)d;
     return cudaGetLastError();
 }
@@ -1207,8 +1213,7 @@ cudaError_t launch_active(const Dev &d, const int *L, int use_list, long long cn
                           const int *parent, const unsigned *sel_ep, const int *att_x, const unsigned *rep_ep,
                           const int *newrep, int *act, int *pold, int *J0, unsigned char *mark, int *aidx,
                           int *aroot, cudaStream_t s) {
-    unsigned g = use_list ? d.grid : gsz((cnt_static + IPT - 1) / IPT);
-    k_active<<<g, BLK, 0, s>>>(L, use_list, cnt_static, ctl, rep, parent, sel_ep, att_x, rep_ep, newrep, act,
+    k_active<<<d.grid_pass, BLK, 0, s>>>(L, use_list, cnt_static, ctl, rep, parent, sel_ep, att_x, rep_ep, newrep, act,
                                 pold, J0, mark, aidx, aroot);
     return cudaGetLastError();
 }

@@ -17,6 +17,7 @@ struct Dev {
     unsigned coop_bfs;
     unsigned coop_et;
     unsigned grid_scan;   // row scan: the co-resident block count
+    unsigned grid_pass;   // vertex passes (affected list, refresh): the co-resident block count
 };
 
 // graph.cu -------------------------------------------------------------
@@ -106,6 +107,7 @@ cudaError_t launch_reverse(const Dev &d, Ctl *ctl, const int *act, const int *po
 cudaError_t launch_labels(int n, const int *rep, int *tmp, int *out, cudaStream_t s);
 
 unsigned coop_blocks_jump(int nsm);
+unsigned grid_vertex_pass(int nsm);
 unsigned coop_blocks_hook(int nsm);
 unsigned coop_blocks_orient(int nsm);
 unsigned coop_blocks_mark(int nsm);
