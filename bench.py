@@ -83,7 +83,9 @@ def workload_config(name, g, b):
     return {"workload": desc, "vertices": int(g.n), "edges": int(g.m), "batch": int(b),
             "step": f"one {b}-edge insert batch + one {b}-edge delete batch",
             "initial_forest": "FIFO BFS from each component's smallest id",
-            "reversal": "euler-tour intervals" if getattr(ARGS, "euler", False) else "pointer-doubling marks",
+            "reversal": ("euler-tour intervals" if getattr(ARGS, "euler", False)
+                         else "walks up to 64 edges, pointer-doubling marks beyond"),
+            "root_search": os.environ.get("DRSF_JUMP", "asynchronous pointer doubling"),
             "l2": "flushed between timed steps (256 MB write)"}
 
 

@@ -144,6 +144,11 @@ DRSF_API drsf_status drsf_set_allocator(drsf_alloc_fn alloc, drsf_free_fn free_f
  * an open-addressing edge index for O(1) deletion.  Synchronises the stream
  * once (to size the CSR).  Without DRSF_VALIDATE, an F that is not a rooted
  * spanning forest of G gives undefined (but memory-safe) results.
+ * The environment variable DRSF_JUMP, read here, selects the root search of
+ * the handle's delete batches: unset, asynchronous pointer doubling (per-warp
+ * slices stepping in place, no grid barrier between steps); "sync",
+ * synchronous doubling rounds; "halving", path-halving walks.  All three give
+ * the same representatives.
  * Errors: DRSF_EINVAL (n out of range, negative m, NULL pointers, an id out
  * of range), DRSF_ENOMEM, DRSF_ECUDA, DRSF_ENOT_FOREST.
  */
