@@ -58,6 +58,18 @@ def test_grid_deep_paths():
     assert st is not None
 
 
+@pytest.mark.parametrize("variant", ["sync", "halving"])
+def test_root_search_variants(variant, monkeypatch):
+    """The selectable root searches of delete batches (synchronous doubling
+    rounds, path-halving walks) give the oracle's forest too; R-MAT-16 and a
+    deep grid (long doubling chains)."""
+    monkeypatch.setenv("DRSF_JUMP", variant)
+    g = workloads.rmat_graph(16, 16, seed=2)
+    run_trajectory(g, [(I, 1000), (D, 1000), (I, 10_000), (D, 10_000)] * 2, seed=3)
+    g = workloads.grid_graph(256, 256, seed=3)
+    run_trajectory(g, [(D, 2000), (I, 2000)] * 2, seed=4, tree_frac=0.9, local=64)
+
+
 def test_deterministic_run_to_run():
     g = workloads.rmat_graph(14, 8, seed=5)
     tr = workloads.Trajectory(g, seed=6)
