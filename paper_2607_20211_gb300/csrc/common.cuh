@@ -119,22 +119,6 @@ __device__ __forceinline__ long long agg_append(u64 *ctr, bool pred) {
     return (long long)(base + __popc(m & ((1u << lane) - 1u)));
 }
 
-// Warp-level pre-reduction of a 64-bit atomicMin: lanes with the same
-// target index combine their values (minimum over the group, taken as the
-// minimum high word, then the minimum low word among lanes holding it) and
-// one lane per group issues the atomic.  Removes the hot-address contention
-// of many lanes hitting one component.
-__device__ __forceinline__ void warp_atomic_min_u64(u64 *arr, int idx, u64 k, bool pred) {
-    unsigned act = __activemask();
-    unsigned m = __ballot_sync(act, pred);
-    if (!pred) return;
-    unsigned grp = __match_any_sync(m, idx);
-    unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;
-    unsigned hmin = __reduce_min_sync(grp, hi);
-    unsigned lmin = __reduce_min_sync(grp, hi == hmin ? lo : 0xFFFFFFFFu);
-    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicMin(&arr[idx], ((u64)hmin << 32) | lmin);
-}
-
 // Pair table: piece pair (min, max) -> minimum edge key between the two
 // pieces.  Probing is bounded; a pair that finds no slot returns false and
 // the caller keeps the edge as a plain candidate instead.
@@ -278,21 +262,6 @@ __device__ __forceinline__ void block_reserve4(u64 *ctr, const bool f[4], long l
         slot[k] = f[k] ? base + off + p[k] : -1;
         off += t[k];
     }
-    __syncthreads();
-}
-
-// The same for two slabs.
-__device__ __forceinline__ void block_reserve2(u64 *ctr, const bool f[2], long long slot[2]) {
-    __shared__ u64 s_rb2;
-    long long packed = (long long)f[0] | ((long long)f[1] << 32);
-    long long tot;
-    long long pre = block_excl_scan_ll(packed, &tot);
-    long long t0 = tot & 0xFFFFFFFFll, t1 = tot >> 32;
-    if (threadIdx.x == 0) s_rb2 = t0 + t1 ? atomicAdd(ctr, (u64)(t0 + t1)) : 0;
-    __syncthreads();
-    long long base = (long long)s_rb2;
-    slot[0] = f[0] ? base + (pre & 0xFFFFFFFFll) : -1;
-    slot[1] = f[1] ? base + t0 + (pre >> 32) : -1;
     __syncthreads();
 }
 

@@ -676,32 +676,6 @@ __global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int 
     if (gtid() == 0) ctl->hook_rounds = r;
 }
 
-// Block-wide exclusive scan of int (BLK threads); *total receives the sum.
-__device__ int block_excl_scan(int v, int *total) {
-    __shared__ int ws[BLK / 32];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) ws[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        int t = lane < BLK / 32 ? ws[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        if (lane < BLK / 32) ws[lane] = t;
-    }
-    __syncthreads();
-    int pre = (w > 0 ? ws[w - 1] : 0) + x - v;
-    *total = ws[BLK / 32 - 1];
-    __syncthreads();
-    return pre;
-}
-
 // Orientation of E_r (Algorithm 2, phase 2).  The replacement edges form a
 // forest over the pieces (the super-forest); each super-tree is rooted at
 // its piece with the smallest root id.  A non-root piece with a single
