@@ -637,7 +637,7 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
         if (h->jump_sync == 2) CK(launch_jump_async(h->dev, h->A, ctl, h->J0, h->act, h->xlist, s));
         CK(launch_jump(h->dev, h->A, 1, 0, ctl, h->parent, h->J0, h->J1, h->rep, rows(h), 1, h->rold, h->wgt,
                        h->heavy, g, h->jump_sync, h->act, h->xlist, h->cutlist, s));
-        prof_end(h, PH_JUMP, 1, s);
+        prof_end(h, PH_JUMP, h->jump_sync == 2 ? 2 : 1, s);   // the asynchronous doubling is a launch of its own
         prof_begin(h, PH_SCAN, s);
         CK(launch_scan_rows(h->dev, rows(h), ctl, g, h->rep, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
         CK(launch_scan_ovf(h->dev, h->ovf, ctl, h->rep, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
