@@ -19,8 +19,11 @@
 //     streams, or threads) race on the array and give wrong results: order
 //     them on one stream.
 //   - The first call on a device looks up the device address of the array
-//     (cudaGetSymbolAddress) with that device current; make the first call
-//     before any stream capture.
+//     (cudaGetSymbolAddress) with that device current and keeps it for the
+//     life of the process; a cudaDeviceReset while the library is loaded is
+//     not supported (the kept address would belong to the old context).
+//   - Every call synchronises its stream and reads a status word back to
+//     the host, so the call cannot be recorded into a CUDA graph.
 #include <climits>
 #include <mutex>
 
@@ -30,7 +33,10 @@
 
 // [0, MAX): jump pointers J; [MAX, 2 MAX): root of each vertex R (written
 // only by that vertex's thread); [2 MAX, 3 MAX): per-tree minimum; then a
-// status word (bit 1: bad parent id, bit 2: walk bound exceeded).
+// status word (bit 1: bad parent id, bit 2: walk bound exceeded, bit 4: a
+// walk ended on a vertex that is not a root of the input, i.e. a cycle).
+// The status word is cleared by a memset in stream order before the first
+// kernel, never inside a multi-block launch that may also set it.
 static __device__ __align__(256) int g_noalloc_scratch[3 * NOALLOC_MAX_N + 64];
 
 namespace {
@@ -39,7 +45,6 @@ int *g_na_ptr[256];   // device address of g_noalloc_scratch per device id
 }
 
 __global__ void k_na_init(const int *parent, int n, int *J, int *mn, int *status) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
         int p = parent[v];
         if (p < 0 || p >= n) {
@@ -55,12 +60,19 @@ __global__ void k_na_init(const int *parent, int n, int *J, int *mn, int *status
 // J[x] only moves to an ancestor of x, so concurrent walks stay correct).
 // J[x] itself may be left pointing at a non-root ancestor by a late halving
 // write of another walk, so the root goes to R[v], which only this thread
-// writes.
-__global__ void k_na_roots(int n, int *J, int *R, int *status) {
+// writes.  On a cycle a halving step can make a cycle vertex point at
+// itself (J[x] = x), which ends walks at a vertex whose input parent is not
+// itself: that is checked against the input and reported as bit 4.
+__global__ void k_na_roots(int n, const int *parent, int *J, int *R, int *status) {
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
         int x = (int)v;
         int root = -1;
-        for (int it = 0; it < (1 << 21); ++it) {
+        // On a forest every step moves x at least two levels up (p is a
+        // proper ancestor of x and gp one of p, whatever other walks wrote),
+        // so a walk ends within depth / 2 + 1 <= n / 2 + 1 steps; a walk
+        // that does not is on a cycle.
+        const int bound = (n >> 1) + 2;
+        for (int it = 0; it < bound; ++it) {
             int p = __ldcg(&J[x]);
             int gp = __ldcg(&J[p]);
             if (p == gp) {
@@ -73,6 +85,9 @@ __global__ void k_na_roots(int n, int *J, int *R, int *status) {
         if (root < 0) {
             atomicOr(status, 2);
             root = (int)v;
+        } else {
+            int pr = parent[root];   // a true root of the input points at itself
+            if (pr != root && pr >= 0 && pr < n) atomicOr(status, 4);
         }
         R[v] = root;
     }
@@ -116,8 +131,12 @@ extern "C" drsf_status drsf_forest_labels_noalloc(int32_t n, const int32_t *pare
     int *J = base, *R = base + NOALLOC_MAX_N, *mn = base + 2 * NOALLOC_MAX_N, *status = base + 3 * NOALLOC_MAX_N;
     cudaStream_t s = (cudaStream_t)stream;
     unsigned g = grid_for(n, BLK, 152u * 16u);
+    if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) {
+        cudaGetLastError();
+        return DRSF_ECUDA;
+    }
     k_na_init<<<g, BLK, 0, s>>>(parent, n, J, mn, status);
-    k_na_roots<<<g, BLK, 0, s>>>(n, J, R, status);
+    k_na_roots<<<g, BLK, 0, s>>>(n, parent, J, R, status);
     k_na_min<<<g, BLK, 0, s>>>(n, R, mn);
     k_na_out<<<g, BLK, 0, s>>>(n, R, mn, labels);
     int st = 0;
