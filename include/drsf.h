@@ -78,7 +78,12 @@ typedef enum { DRSF_INSERT = 0, DRSF_DELETE = 1 } drsf_op;
 enum {
     /* Minimum-key replacement edges and smallest-root-id super-roots: the
      * result is a function of the inputs alone (bit-identical parent arrays
-     * run to run).  Always on in this version; accepted for compatibility. */
+     * run to run).  In the paper, which cross edge of a super-edge wins is
+     * left to races between threads (Section III-A/B).  Here the
+     * minimum-key rule is the only mode: it costs one 64-bit atomic minimum
+     * per candidate, the same single atomic a first-winner hook would take,
+     * so a non-deterministic mode would have nothing to gain and none is
+     * built.  The flag is accepted and ignored. */
     DRSF_DETERMINISTIC = 1u,
     /* drsf_create checks on the device that parent is a rooted spanning
      * forest of G and fails with DRSF_ENOT_FOREST otherwise (synchronises). */
@@ -90,7 +95,14 @@ enum {
     DRSF_EULER_REVERSAL = 4u
 };
 
-/* Per-batch counters of the last applied batch (drsf_stats). */
+/* Per-batch counters of the last applied batch (drsf_stats).  They count
+ * the steps of Algorithm 1 (Section II-D) for one batch: the graph update
+ * (applied, dropped), the cut of deleted tree edges and the pointer jumping
+ * for representatives (tree_cut, affected, jump_rounds, jump_visits), the
+ * cross-edge scan and hook-and-compress for replacement edges (Section II-A,
+ * III-B: detached, scanned, candidates, hook_rounds, replacement), the
+ * Euler-tour orientation (rank_rounds) and the path reversal (Section II-C,
+ * III-C/D: active, reversed, mark_rounds). */
 typedef struct {
     int64_t batch_len;     /* |B| as passed */
     int64_t self_loops;    /* dropped: u == v */
@@ -132,8 +144,8 @@ typedef void (*drsf_free_fn)(void *ptr, drsf_stream stream, void *ctx);
 DRSF_API drsf_status drsf_set_allocator(drsf_alloc_fn alloc, drsf_free_fn free_fn, void *ctx);
 
 /*
- * drsf_create -- build the device state for G and F (problem box, Section I:
- * "an undirected graph G and a rooted spanning forest F of G").
+ * drsf_create -- build the device state for the problem's inputs (problem
+ * box, Section I): the undirected graph G and its rooted spanning forest F.
  *   n       number of vertices, 1 <= n <= 2^31 - 1
  *   edges   device, int32[2*m], the edge list of G; self-loops and repeated
  *           pairs are dropped; m may be 0 (edges may then be NULL)
@@ -179,8 +191,12 @@ DRSF_API drsf_status drsf_apply(drsf_handle h, drsf_op op, const int32_t *batch,
 DRSF_API drsf_status drsf_apply_host(drsf_handle h, drsf_op op, const int32_t *batch, int64_t len,
                             drsf_stream stream);
 
-/* drsf_parent -- copy F' (int32[n], parent[r] == r at roots) to device
- * buffer `out` on `stream`.  Does not synchronise. */
+/* drsf_parent -- the output of the D-RSF problem (problem box, Section I):
+ * the rooted spanning forest F' of the updated graph G', as parent
+ * pointers.  Copies
+ * int32[n] (parent[r] == r at roots) to device buffer `out` on `stream`.
+ * Does not synchronise.  Errors: DRSF_EINVAL (NULL handle or out),
+ * DRSF_EPOISONED, DRSF_ECUDA. */
 DRSF_API drsf_status drsf_parent(drsf_handle h, int32_t *out, drsf_stream stream);
 
 /*
@@ -191,8 +207,10 @@ DRSF_API drsf_status drsf_parent(drsf_handle h, int32_t *out, drsf_stream stream
  */
 DRSF_API drsf_status drsf_labels(drsf_handle h, int32_t *out, drsf_stream stream);
 
-/* drsf_stats -- counters of the last batch; synchronises `stream`; returns
- * any latched device error. */
+/* drsf_stats -- the counters of the last batch's Algorithm 1 steps (see
+ * drsf_batch_stats) into host struct `out`; synchronises `stream`; returns
+ * any latched device error (DRSF_EINVAL once for a skipped batch with an
+ * out-of-range id, DRSF_ETIMEOUT / DRSF_EPOISONED for a poisoned handle). */
 DRSF_API drsf_status drsf_stats(drsf_handle h, drsf_batch_stats *out, drsf_stream stream);
 
 /* drsf_sync -- synchronise `stream` and return any latched device error. */
@@ -264,13 +282,16 @@ DRSF_API drsf_status drsf_selftest_barrier_timeout(drsf_stream stream);
  *   n       1 <= n <= DRSF_NOALLOC_MAX_N, else DRSF_EINVAL (nothing enqueued)
  *   parent  device, int32[n], parent[r] == r at roots
  *   labels  device, int32[n], output
- * Synchronises `stream`; returns DRSF_EINVAL if parent has an id outside
- * [0, n) or a cycle.  Every call on a device shares the scratch array (it
- * keeps the last call's contents; each call re-initialises what it reads):
- * calls that overlap on the GPU race, so order them on one stream.  The
- * first call on a device resolves the array's device address with that
- * device current; make it before any stream capture.  The array (12 MiB)
- * stays allocated on every GPU that loads the library until exit.
+ * Synchronises `stream` (it reads a status word back), so it cannot be
+ * recorded into a CUDA graph; returns DRSF_EINVAL if parent has an id
+ * outside [0, n) or a cycle.  Every call on a device shares the scratch
+ * array (it keeps the last call's contents; each call re-initialises what
+ * it reads, the status word by a memset in stream order): calls that
+ * overlap on the GPU race, so order them on one stream.  The first call on
+ * a device resolves the array's device address with that device current
+ * and keeps it; a cudaDeviceReset while the library is loaded is not
+ * supported.  The array (12 MiB) stays allocated on every GPU that loads
+ * the library until exit.
  */
 #define DRSF_NOALLOC_MAX_N (1 << 20)
 DRSF_API drsf_status drsf_forest_labels_noalloc(int32_t n, const int32_t *parent, int32_t *labels,
