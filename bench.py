@@ -239,7 +239,8 @@ def plan(g, cfg, steps, b, seed):
     f = drsf.DynamicForest(g.n, torch.from_numpy(g.edges()).cuda(), torch.from_numpy(g.parent).cuda())
     tr = workloads.Trajectory(g, seed, tree_frac=cfg["tree_frac"], local=cfg["local"])
     out = []
-    for _ in range(steps):
+    first = []   # parent arrays after the first step's two batches
+    for k in range(steps):
         pair = []
         for op in (0, 1):
             batch = tr.next_batch(op, b)
@@ -248,10 +249,12 @@ def plan(g, cfg, steps, b, seed):
             par = f.parent().cpu().numpy()
             tr.advance(batch, op, par)
             pair.append((batch, st))
+            if k == 0:
+                first.append(par.copy())
         out.append(pair)
     final = f.parent().cpu().numpy()
     f.close()
-    return out, final
+    return out, final, first
 
 
 def run_ours(args, rank, ws, local):
@@ -262,7 +265,7 @@ def run_ours(args, rank, ws, local):
     g, cfg = make_graph(args.workload)
     b = args.batch or cfg["batch"]
     K, W = args.steps, args.warmup
-    steps, final_plan = plan(g, cfg, W + K, b, seed=5)
+    steps, final_plan, first_parents = plan(g, cfg, W + K, b, seed=5)
     dev_batches = [[torch.from_numpy(p[0]).cuda() for p in s] for s in steps]
     edges_d = torch.from_numpy(g.edges()).cuda()
     parent_d = torch.from_numpy(g.parent).cuda()
@@ -341,6 +344,11 @@ def run_ours(args, rank, ws, local):
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "algorithmic_bytes_per_launch": int(per_launch_bytes),
                 "ms_per_launch": round(per_launch_ms, 5)}
+    # whole step: every phase's algorithmic bytes over the timed step time
+    step_bytes = sum(pbytes.values()) / K
+    step_gbs = step_bytes / (secs / K) / 1e9 if secs > 0 else 0.0
+    roofline["step"] = {"algorithmic_bytes": int(step_bytes), "achieved": round(step_gbs, 1),
+                        "frac": round(step_gbs / peak, 4), "ms": round(secs / K * 1e3, 4)}
     step_total_ms = sum(v[0] for v in phases.values())
     phase_table = {}
     for oname in ("insert", "delete"):
@@ -384,8 +392,9 @@ def run_ours(args, rank, ws, local):
     clocks = clk.stop()
 
     cpu = None
+    parity0 = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(g, steps)
+        cpu, parity0 = cpu_baseline(g, steps, first_parents)
     if rank != 0:
         return
     lat = sorted(ins_ms + del_ms)
@@ -408,6 +417,7 @@ def run_ours(args, rank, ws, local):
                            "x_delete_batch": round(float(np.median(st_ms[1:])) / float(np.median(del_ms)), 2)},
         "roofline": roofline, "phases": phase_table, "batch_stats": batch_stats, "e2e": e2e,
         "cpu_baseline": cpu,
+        "parity_step0": parity0,
         "gpu_launches": int(sum(v[1] for v in phases.values())),
         "clocks": clocks,
     }
@@ -607,13 +617,16 @@ def run_serving(args, rank, ws, local):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(g, steps):
+def cpu_baseline(g, steps, gpu_parents):
     """The serial oracle on the host cores, one step of the same trajectory
-    (the first insert + delete batch from the initial state)."""
+    (the first insert + delete batch from the initial state).  Its results
+    are also compared with the GPU's parent arrays after the same two
+    batches (True when both are bit-identical)."""
     import oracle
     keys, par = g.keys, g.parent
     t = 0.0
     applied = 0
+    same = True
     for op in (0, 1):
         batch = steps[0][op][0]
         t0 = time.perf_counter()
@@ -621,9 +634,10 @@ def cpu_baseline(g, steps):
         t += time.perf_counter() - t0
         applied += r.stats["applied"]
         keys, par = r.keys, r.parent
-    return {"value": round(applied / t, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 step (insert + delete, {len(steps[0][0][0])} edges each) of the same trajectory",
-            "seconds": round(t, 3)}
+        same = same and bool(np.array_equal(par, gpu_parents[op]))
+    return ({"value": round(applied / t, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+             "sample": f"1 step (insert + delete, {len(steps[0][0][0])} edges each) of the same trajectory",
+             "seconds": round(t, 3)}, same)
 
 
 # ------------------------------------------------------------ reference arm

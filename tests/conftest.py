@@ -11,3 +11,11 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long-running (full-size workloads)")
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _oracle_pool_teardown():
+    yield
+    mod = sys.modules.get("tests.oracle_pool")
+    if mod is not None:
+        mod.shutdown()

@@ -64,3 +64,26 @@ def _tiny_graph(n, edges, parent):
     g.name, g.n, g.keys, g.W = "tiny", n, keys, 0
     g.parent = np.array(parent, np.int32) if parent is not None else workloads.bfs_forest(n, keys)
     return g
+
+
+def run_trajectory_pooled(g, schedule, seed, tree_frac=0.5, local=0, labels=True, flags=drsf.DETERMINISTIC):
+    """As run_trajectory, for long or large trajectories: the GPU runs the
+    whole schedule and every batch is checked against the oracle in the
+    process pool of tests/oracle_pool.py (same checks, side by side).
+    Returns the number of batches checked."""
+    from tests.oracle_pool import TrajectoryCheck
+    chk = TrajectoryCheck(g.n, g.keys, g.parent)
+    f = make_forest(g, flags=flags)
+    tr = workloads.Trajectory(g, seed, tree_frac=tree_frac, local=local)
+    try:
+        for op, b in schedule:
+            batch = tr.next_batch(op, b)
+            f.apply(op, dev_tensor(batch.reshape(-1, 2)))
+            par = f.parent().cpu().numpy()
+            st = f.stats()
+            lab = f.labels().cpu().numpy() if labels else None
+            chk.add(op, batch, par, st, lab)
+            tr.advance(batch, op, par)
+    finally:
+        f.close()
+    return chk.result()

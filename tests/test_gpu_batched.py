@@ -47,3 +47,39 @@ def test_union_equals_per_graph():
         assert np.array_equal(f.parent().cpu().numpy(), r.parent), i
         f.close()
     fu.close()
+
+
+def test_union_256_graphs_config_shape():
+    """The batched configuration at its real shape: 256 graphs (n
+    log-uniform in [1K, 256K], half Erdos-Renyi, half R-MAT, seed 4), two
+    steps of one insert batch and one delete batch per graph (1-10% of m,
+    60/40), applied as union batches; every graph's forest and labels after
+    every batch are checked against its own oracle run (process pool)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from tests.oracle_pool import TrajectoryCheck
+    drsf.build()
+    graphs = workloads.batched_graphs(256, seed=4)
+    U = workloads.Union(graphs)
+    fu = drsf.DynamicForest(U.n, dev_tensor(workloads.keys_to_edges(U.keys)), dev_tensor(U.parent))
+    trs = [workloads.Trajectory(g, seed=(4 << 20) + i) for i, g in enumerate(graphs)]
+    chks = [TrajectoryCheck(g.n, g.keys, g.parent) for g in graphs]
+    try:
+        for step in range(2):
+            budgets = workloads.batched_budgets(graphs, seed=4 + 7919 * step)
+            for op in (drsf.INSERT, drsf.DELETE):
+                per = [tr.next_batch(op, b[op]) for tr, b in zip(trs, budgets)]
+                fu.apply(op, dev_tensor(np.concatenate([U.shift(i, b) for i, b in enumerate(per)])))
+                st = fu.stats()
+                assert st["applied"] == sum(len(b) for b in per)
+                parts = U.split(fu.parent().cpu().numpy())
+                labs = U.split(fu.labels().cpu().numpy())
+                for i, (tr, b, p, lab) in enumerate(zip(trs, per, parts, labs)):
+                    # per-graph counters are not separable from the union's;
+                    # check the per-graph forest, labels and checker only
+                    chks[i].add(op, b, p, None, lab)
+                    tr.advance(b, op, p)
+        for c in chks:
+            c.result()
+    finally:
+        fu.close()

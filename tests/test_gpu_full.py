@@ -1,13 +1,14 @@
 """GPU parity at the full sizes of the configurations (R-MAT scale 20 and
 22, the 4096 x 4096 grid), through the same C-ABI path the benchmark times.
-The oracle handles these sizes in seconds per batch, so every output is
-compared, not a sample."""
+Every batch of every trajectory is compared with the oracle (parent arrays
+bit for bit, labels, the exact checker, the counters); the oracle checks run
+side by side in a process pool (tests/oracle_pool.py)."""
 import pytest
 import torch
 
 import paper_2607_20211_gb300 as drsf
 import workloads
-from tests.gpu_util import run_trajectory
+from tests.gpu_util import run_trajectory_pooled
 
 pytestmark = pytest.mark.gpu
 
@@ -22,20 +23,32 @@ def _cuda():
 
 
 def test_rmat20_batch_sizes():
-    """R-MAT scale 20, edge factor 16, seed 2: insert/delete at 10K, 100K, 1M."""
+    """R-MAT scale 20, edge factor 16, seed 2: for each batch size 10K, 100K
+    and 1M in turn, 20 batches alternating insert and delete (deletes half
+    tree edges) on the evolving graph."""
     g = workloads.rmat_graph(20, 16, seed=2)
-    run_trajectory(g, [(I, 10_000), (D, 10_000), (I, 100_000), (D, 100_000), (I, 1_000_000),
-                       (D, 1_000_000)], seed=2, labels=False)
+    sched = [(I if k % 2 == 0 else D, b) for b in (10_000, 100_000, 1_000_000) for k in range(20)]
+    assert run_trajectory_pooled(g, sched, seed=2) == 60
 
 
 def test_grid4096_deep():
     """4096 x 4096 grid, p = 0.6, 0.1% shortcuts, seed 3: 100K deletes with 90%
-    tree edges, then 100K local inserts."""
+    tree edges (deep re-rooted paths), then 100K local inserts, twice."""
     g = workloads.grid_graph(4096, 4096, seed=3)
-    run_trajectory(g, [(D, 100_000), (I, 100_000)], seed=3, tree_frac=0.9, local=64, labels=False)
+    assert run_trajectory_pooled(g, [(D, 100_000), (I, 100_000)] * 2, seed=3, tree_frac=0.9, local=64) == 4
 
 
-def test_rmat22_100k():
-    """R-MAT scale 22 (the benchmark workload), 100K insert then 100K delete."""
+def test_grid4096_euler_reversal():
+    """The same deep-grid batches with the Euler-tour path reversal
+    (Algorithm 3) in place of walks and doubling marks."""
+    g = workloads.grid_graph(4096, 4096, seed=3)
+    assert run_trajectory_pooled(g, [(D, 100_000), (I, 100_000)], seed=3, tree_frac=0.9, local=64,
+                                 flags=drsf.DETERMINISTIC | drsf.EULER_REVERSAL) == 2
+
+
+def test_rmat22_bench_trajectory():
+    """R-MAT scale 22 (the benchmark workload), the benchmark's own
+    trajectory (seed 5): its first 8 steps of one 100K insert batch and one
+    100K delete batch."""
     g = workloads.rmat_graph(22, 16, seed=5)
-    run_trajectory(g, [(I, 100_000), (D, 100_000)], seed=5, labels=False)
+    assert run_trajectory_pooled(g, [(I, 100_000), (D, 100_000)] * 8, seed=5) == 16
