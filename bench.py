@@ -309,6 +309,7 @@ def run_ours(args, rank, ws, local):
     f.close()
     if not np.array_equal(final, final_plan):
         raise RuntimeError("timed replay diverged from the planning pass")
+    variants = replacement_variants(g, edges_d, parent_d, dev_batches, W, min(K, 5), flush, stream)
     ins_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
     del_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
     step_ms = [i + d for i, d in zip(ins_ms, del_ms)]
@@ -415,6 +416,7 @@ def run_ours(args, rank, ws, local):
                                    "on the final graph, same GPU",
                            "x_insert_batch": round(float(np.median(st_ms[1:])) / float(np.median(ins_ms)), 2),
                            "x_delete_batch": round(float(np.median(st_ms[1:])) / float(np.median(del_ms)), 2)},
+        "replacement_variants": variants,
         "roofline": roofline, "phases": phase_table, "batch_stats": batch_stats, "e2e": e2e,
         "cpu_baseline": cpu,
         "parity_step0": parity0,
@@ -422,6 +424,36 @@ def run_ours(args, rank, ws, local):
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
+
+
+def replacement_variants(g, edges_d, parent_d, dev_batches, W, K, flush, stream):
+    """Insert and delete batch times with each replacement-edge variant
+    forced (supergraph reduction vs hooking on every cross edge, Section
+    III), replaying the same first W + K steps on fresh handles."""
+    import torch
+    import paper_2607_20211_gb300 as drsf
+    out = {}
+    for name, flag in (("sg", drsf.REPL_SG), ("hs", drsf.REPL_HS)):
+        f = drsf.DynamicForest(g.n, edges_d, parent_d, flags=drsf.DETERMINISTIC | flag)
+        ms = {0: [], 1: []}
+        cands = {0: [], 1: []}
+        for k in range(W + K):
+            for op in (0, 1):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                f.apply(op, dev_batches[k][op])
+                e1.record(stream)
+                st = f.stats()
+                if k >= W:
+                    ms[op].append(e0.elapsed_time(e1))
+                    cands[op].append(st["candidates"])
+        f.close()
+        out[name] = {"insert_ms": round(float(np.median(ms[0])), 4), "delete_ms": round(float(np.median(ms[1])), 4),
+                     "insert_candidates": int(np.mean(cands[0])), "delete_candidates": int(np.mean(cands[1]))}
+    out["what"] = (f"median batch time over {K} steps after {W} warm-up, each variant forced; the default "
+                   "picks per batch (SG when the key edges exceed n/16)")
+    return out
 
 
 def run_batched(args, rank, ws, local):

@@ -92,7 +92,21 @@ enum {
      * of the re-rooted trees (Algorithm 3).  Default: paths of up to 64
      * edges are reversed by one walking thread each, longer ones through
      * pointer-doubling marks.  Same result. */
-    DRSF_EULER_REVERSAL = 4u
+    DRSF_EULER_REVERSAL = 4u,
+    /* Replacement-edge variant (Section III).  DRSF_REPL_SG, the supergraph
+     * variant (Section III-A): the cross edges are reduced to one super-edge
+     * per pair of trees (its minimum-key cross edge, through a hash table
+     * keyed by the pair of roots), and the hooking then runs on the
+     * supergraph.  DRSF_REPL_HS, hooking and shortcutting (Section III-B):
+     * the hooking runs on every cross edge.  Neither flag (or both): chosen
+     * per batch by comparing the number of key edges |M| with n, as the
+     * paper's comparison of the two does (Section V, influencing factors):
+     * SG when |M| > n / 16, where |M| is the batch length for an insert and
+     * the non-tree edges of G (live edges - n) for a delete.  The result is
+     * the same either way (the minimum-key forest does not depend on how
+     * parallel super-edges are reduced). */
+    DRSF_REPL_SG = 8u,
+    DRSF_REPL_HS = 16u
 };
 
 /* Per-batch counters of the last applied batch (drsf_stats).  They count
@@ -134,6 +148,8 @@ typedef struct {
     int64_t overflow;      /* edges held outside their CSR row (slack exhausted) */
     int64_t rebuilds;      /* CSR / index rebuilds so far */
     int64_t jump_visits;   /* vertex visits summed over the pointer-jumping steps */
+    int64_t supergraph;    /* 1: the batch took the supergraph (SG) variant,
+                              0: hooking on every cross edge (HS) */
 } drsf_batch_stats;
 
 /* Allocator hooks.  alloc(bytes, stream, ctx) returns device memory or NULL;
@@ -150,7 +166,8 @@ DRSF_API drsf_status drsf_set_allocator(drsf_alloc_fn alloc, drsf_free_fn free_f
  *   edges   device, int32[2*m], the edge list of G; self-loops and repeated
  *           pairs are dropped; m may be 0 (edges may then be NULL)
  *   parent  device, int32[n], F as parent pointers (parent[r] == r at roots)
- *   flags   DRSF_DETERMINISTIC | DRSF_VALIDATE
+ *   flags   DRSF_DETERMINISTIC | DRSF_VALIDATE | DRSF_EULER_REVERSAL |
+ *           DRSF_REPL_SG | DRSF_REPL_HS
  *   out     receives the handle (NULL on failure)
  * The graph is stored as a slack CSR (int64 row offsets, int32 columns) with
  * an open-addressing edge index for O(1) deletion.  Synchronises the stream

@@ -27,7 +27,7 @@ import torch
 from . import build as _build_mod
 
 INSERT, DELETE = 0, 1
-DETERMINISTIC, VALIDATE, EULER_REVERSAL = 1, 2, 4
+DETERMINISTIC, VALIDATE, EULER_REVERSAL, REPL_SG, REPL_HS = 1, 2, 4, 8, 16
 
 OK, EINVAL, ENOMEM, ECUDA, ENOT_FOREST, ETIMEOUT, EPOISONED = range(7)
 
@@ -47,7 +47,7 @@ class BatchStats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in (
         "batch_len", "self_loops", "dropped", "applied", "tree_cut", "affected", "detached", "scanned",
         "candidates", "hook_rounds", "replacement", "rank_rounds", "active", "reversed", "mark_rounds",
-        "jump_rounds", "edges", "overflow", "rebuilds", "jump_visits")]
+        "jump_rounds", "edges", "overflow", "rebuilds", "jump_visits", "supergraph")]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -34,6 +34,7 @@ struct drsf_ctx {
     bool poisoned = false;
     int jump_sync = 2;   // root search: 2 asynchronous doubling, 1 synchronous rounds, 0 path halving
     int pending_einval = 0;
+    int last_sg = 0;     // the last batch took the supergraph variant
 
     Ctl *ctl = nullptr;
     Ctl *ctl_host = nullptr;   // pinned
@@ -598,11 +599,28 @@ drsf_status drsf_create(int32_t n, const int32_t *edges, int64_t m, const int32_
     return DRSF_OK;
 }
 
+// Replacement-edge variant of a batch (Section III): the supergraph (SG)
+// reduction of parallel cross edges, or hooking on every cross edge (HS).
+// A flag forces one; otherwise the key-edge count |M| is compared with n
+// (Section V: HS suits |M| >> n in the paper's implementations, SG the
+// opposite; here the hooking's cost follows the candidate count, so the
+// supergraph's reduction pays off when the key edges outnumber the
+// vertices).  |M| is the batch for an insert and the non-tree edges of G
+// for a delete, from the host-side bound on live edges (no device read).
+static bool use_supergraph(const drsf_ctx *h, int op, long long len) {
+    const bool sg = (h->flags & DRSF_REPL_SG) != 0, hs = (h->flags & DRSF_REPL_HS) != 0;
+    if (sg != hs) return sg;
+    long long keys = op == DRSF_INSERT ? len : std::max<long long>(0, h->occ_bound - (long long)h->n);
+    return keys > (long long)h->n / 16;
+}
+
 static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t len, cudaStream_t s) {
     drsf_status st = ensure_batch(h, len, s);
     if (st) return st;
     st = storage_check(h, op, len, s);
     if (st) return st;
+    const bool sg = use_supergraph(h, op, len);
+    h->last_sg = sg ? 1 : 0;
     Ctl *ctl = h->ctl;
     Csr g{h->off, h->used, h->col};
     if (h->prof_on) {
@@ -620,9 +638,10 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
         CK(launch_ins_claim(batch, len, h->ix, ctl, h->nkey, h->nslot, s));
         prof_end(h, PH_INS_CLAIM, len > 0 ? 1 : 0, s);
         prof_begin(h, PH_INS_PLACE, s);
-        CK(launch_ins_place(h->dev, h->nkey, h->nslot, ctl, g, h->ix, h->ovf, h->ovf_cap, h->rep, h->ck[0],
-                            h->ca[0], h->cb[0], h->cand_cap, s));
-        prof_end(h, PH_INS_PLACE, 1, s);
+        CK(launch_ins_place(h->dev, h->nkey, h->nslot, ctl, g, h->ix, h->ovf, h->ovf_cap, h->rep, sg, h->pt,
+                            h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
+        if (sg) CK(launch_pairs_compact(h->dev, ctl, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
+        prof_end(h, PH_INS_PLACE, sg ? 2 : 1, s);
     } else {
         // Algorithm 1, delete: remove B, cut tree edges, re-label the cut trees
         prof_begin(h, PH_DEL_CLAIM, s);
@@ -639,10 +658,11 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
                        h->heavy, g, h->jump_sync, h->act, h->xlist, h->cutlist, s));
         prof_end(h, PH_JUMP, h->jump_sync == 2 ? 2 : 1, s);   // the asynchronous doubling is a launch of its own
         prof_begin(h, PH_SCAN, s);
-        CK(launch_scan_rows(h->dev, rows(h), ctl, g, h->rep, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
-        CK(launch_scan_ovf(h->dev, h->ovf, ctl, h->rep, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
-        CK(launch_pairs_compact(h->dev, ctl, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
-        prof_end(h, PH_SCAN, 3, s);
+        CK(launch_scan_rows(h->dev, rows(h), ctl, g, h->rep, sg, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap,
+                            s));
+        CK(launch_scan_ovf(h->dev, h->ovf, ctl, h->rep, sg, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
+        if (sg) CK(launch_pairs_compact(h->dev, ctl, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
+        prof_end(h, PH_SCAN, sg ? 3 : 2, s);
     }
     prof_begin(h, PH_HOOK, s);
     CK(launch_boruvka(h->dev, ctl, h->ck[0], h->ca[0], h->cb[0], h->ck[1], h->ca[1], h->cb[1], h->comp, h->best0,
@@ -833,6 +853,7 @@ drsf_status drsf_stats(drsf_handle h, drsf_batch_stats *out, drsf_stream stream)
     out->overflow = (int64_t)c.ovf_count;
     out->rebuilds = h->rebuilds;
     out->jump_visits = c.jump_visits;
+    out->supergraph = h->last_sg;
     return latched(h);
 }
 

@@ -237,9 +237,14 @@ __device__ __forceinline__ int row_slot(int *used, int r) {
 // Insert, step 2: append each new edge to both CSR rows (warp-aggregated
 // row cursors are per row, so plain atomics); an edge whose row is full goes
 // whole to the overflow list.  The cross test of the insert case (M = B,
-// Algorithm 1) is fused here: rep[u] != rep[v] makes a candidate.
+// Algorithm 1) is fused here: rep[u] != rep[v] makes a candidate.  With SG
+// (the supergraph variant, Section III-A) a candidate goes into the pair
+// table instead, which keeps the minimum key per pair of trees (one
+// super-edge per pair; k_pairs_compact then lists them); without it (HS,
+// Section III-B) every cross edge is a candidate of the hooking.
+template <bool SG>
 __global__ void k_ins_place(const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, Index ix, u64 *ovf, u64 ovf_cap,
-                            const int *rep, u64 *ck, int *ca, int *cb, u64 cand_cap) {
+                            const int *rep, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap) {
     if (*(volatile int *)&ctl->skip) return;
     long long nb = (long long)ctl->nb;
     // block-uniform loop: the candidate append is aggregated per block
@@ -279,6 +284,7 @@ __global__ void k_ins_place(const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, 
             ra = rep[a];
             rb = rep[b];
             cross = ra != rb;
+            if (SG && cross) cross = !pair_min(pt.pk, pt.mk, pt.mask, ra, rb, k);   // no slot: plain candidate
         }
         long long p = block_append(&ctl->ncand, cross);
         if (cross) {
@@ -383,8 +389,11 @@ __global__ void k_del_claim(const int *batch, long long len, Index ix, Csr g, u6
 // with the minimum key, which is the only one that can be in the minimum
 // spanning forest: lanes holding the same piece pair take the minimum
 // first, then one lane updates the pair table.  A pair that finds no table
-// slot is emitted as a plain candidate.  Entry positions are below 2^32, so
-// the tile arithmetic is 32-bit.
+// slot is emitted as a plain candidate.  This reduction is the supergraph
+// variant's super-edge dedupe (SG, Section III-A); with SG false (HS,
+// Section III-B) every cross edge is emitted as a candidate of the hooking.
+// Entry positions are below 2^32, so the tile arithmetic is 32-bit.
+template <bool SG>
 __global__ void k_scan_lb(RowList rl, Ctl *ctl, Csr g, const int *rep, PairTable pt, u64 *ck, int *ca, int *cb,
                           u64 cand_cap) {
     if (*(volatile int *)&ctl->skip) return;
@@ -435,7 +444,10 @@ __global__ void k_scan_lb(RowList rl, Ctl *ctl, Csr g, const int *rep, PairTable
         if (!m) continue;
         bool raw = false;
         u64 key = 0;
-        if (emit) {
+        if (!SG) {
+            raw = emit;
+            key = ekey((uint32_t)u, (uint32_t)x);
+        } else if (emit) {
             // one piece pair for the whole warp is the common case (a hub
             // row against one other piece): no match needed then
             const int ld = __ffs(m) - 1;
@@ -473,11 +485,12 @@ __global__ void k_scan_lb(RowList rl, Ctl *ctl, Csr g, const int *rep, PairTable
             }
         }
     }
-    if (cpair != EMPTY_KEY) atomicMin(&pt.mk[cslot], cmin);
+    if (SG && cpair != EMPTY_KEY) atomicMin(&pt.mk[cslot], cmin);
 }
 
 // Delete, cross-edge scan of the overflow list (edges outside their rows),
-// through the same pair table.
+// through the same pair table (SG) or straight to the candidates (HS).
+template <bool SG>
 __global__ void k_scan_ovf(const u64 *ovf, Ctl *ctl, const int *rep, PairTable pt, u64 *ck, int *ca, int *cb,
                            u64 cand_cap) {
     if (*(volatile int *)&ctl->skip) return;
@@ -489,7 +502,7 @@ __global__ void k_scan_ovf(const u64 *ovf, Ctl *ctl, const int *rep, PairTable p
         if (k != TOMB_KEY) {
             ra = rep[klo(k)];
             rb = rep[khi(k)];
-            if (ra != rb) raw = !pair_min(pt.pk, pt.mk, pt.mask, ra, rb, k);
+            if (ra != rb) raw = !SG || !pair_min(pt.pk, pt.mk, pt.mask, ra, rb, k);
         }
         long long p = agg_append(&ctl->ncand, raw);
         if (raw) {
@@ -653,9 +666,12 @@ cudaError_t launch_ins_claim(const int *batch, long long len, Index ix, Ctl *ctl
     return cudaGetLastError();
 }
 cudaError_t launch_ins_place(const Dev &d, const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, Index ix,
-                             u64 *ovf, u64 ovf_cap, const int *rep, u64 *ck, int *ca, int *cb, u64 cand_cap,
-                             cudaStream_t s) {
-    k_ins_place<<<d.grid, BLK, 0, s>>>(nkey, nslot, ctl, g, ix, ovf, ovf_cap, rep, ck, ca, cb, cand_cap);
+                             u64 *ovf, u64 ovf_cap, const int *rep, bool sg, PairTable pt, u64 *ck, int *ca, int *cb,
+                             u64 cand_cap, cudaStream_t s) {
+    if (sg)
+        k_ins_place<true><<<d.grid, BLK, 0, s>>>(nkey, nslot, ctl, g, ix, ovf, ovf_cap, rep, pt, ck, ca, cb, cand_cap);
+    else
+        k_ins_place<false><<<d.grid, BLK, 0, s>>>(nkey, nslot, ctl, g, ix, ovf, ovf_cap, rep, pt, ck, ca, cb, cand_cap);
     return cudaGetLastError();
 }
 cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u64 *ovf, int *parent,
@@ -665,22 +681,29 @@ cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u
     k_del_claim<<<gsz(len), BLK, 0, s>>>(batch, len, ix, g, ovf, parent, rep, ctl, aff_ep, cut_ep, cutlist, w);
     return cudaGetLastError();
 }
-cudaError_t launch_scan_rows(const Dev &d, RowList rl, Ctl *ctl, Csr g, const int *rep, PairTable pt, u64 *ck,
-                             int *ca, int *cb, u64 cand_cap, cudaStream_t s) {
-    k_scan_lb<<<d.grid_scan, BLK, 0, s>>>(rl, ctl, g, rep, pt, ck, ca, cb, cand_cap);
+cudaError_t launch_scan_rows(const Dev &d, RowList rl, Ctl *ctl, Csr g, const int *rep, bool sg, PairTable pt,
+                             u64 *ck, int *ca, int *cb, u64 cand_cap, cudaStream_t s) {
+    if (sg)
+        k_scan_lb<true><<<d.grid_scan, BLK, 0, s>>>(rl, ctl, g, rep, pt, ck, ca, cb, cand_cap);
+    else
+        k_scan_lb<false><<<d.grid_scan, BLK, 0, s>>>(rl, ctl, g, rep, pt, ck, ca, cb, cand_cap);
     return cudaGetLastError();
 }
 // Every warp of the row scan takes an equal share of the tiles, so the grid
 // is exactly the blocks that are resident at once (no second wave).
 unsigned scan_grid(int nsm) {
     int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k_scan_lb, BLK, 0) != cudaSuccess || per < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k_scan_lb<true>, BLK, 0) != cudaSuccess ||
+        per < 1)
         per = 1;
     return (unsigned)(per * nsm);
 }
-cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, PairTable pt, u64 *ck, int *ca,
-                            int *cb, u64 cand_cap, cudaStream_t s) {
-    k_scan_ovf<<<d.nsm * 2, BLK, 0, s>>>(ovf, ctl, rep, pt, ck, ca, cb, cand_cap);
+cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, bool sg, PairTable pt, u64 *ck,
+                            int *ca, int *cb, u64 cand_cap, cudaStream_t s) {
+    if (sg)
+        k_scan_ovf<true><<<d.nsm * 2, BLK, 0, s>>>(ovf, ctl, rep, pt, ck, ca, cb, cand_cap);
+    else
+        k_scan_ovf<false><<<d.nsm * 2, BLK, 0, s>>>(ovf, ctl, rep, pt, ck, ca, cb, cand_cap);
     return cudaGetLastError();
 }
 cudaError_t launch_pairs_compact(const Dev &d, Ctl *ctl, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap,

@@ -32,9 +32,7 @@ cudaError_t launch_fill(const u64 *dkey, const u64 *dslot, long long m, Csr g, I
 cudaError_t launch_validate_batch(const int *batch, long long len, int n, Ctl *ctl, cudaStream_t s);
 cudaError_t launch_ins_claim(const int *batch, long long len, Index ix, Ctl *ctl, u64 *nkey, u64 *nslot,
                              cudaStream_t s);
-cudaError_t launch_ins_place(const Dev &d, const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, Index ix,
-                             u64 *ovf, u64 ovf_cap, const int *rep, u64 *ck, int *ca, int *cb, u64 cand_cap,
-                             cudaStream_t s);
+
 cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u64 *ovf, int *parent,
                              const int *rep, Ctl *ctl, unsigned *aff_ep, unsigned *cut_ep, int *cutlist,
                              unsigned *w, cudaStream_t s);
@@ -55,10 +53,15 @@ struct PairTable {
     u64 *mk;   // minimum edge key of the pair
     u64 mask;
 };
-cudaError_t launch_scan_rows(const Dev &d, RowList rl, Ctl *ctl, Csr g, const int *rep, PairTable pt, u64 *ck,
-                             int *ca, int *cb, u64 cand_cap, cudaStream_t s);
-cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, PairTable pt, u64 *ck, int *ca,
-                            int *cb, u64 cand_cap, cudaStream_t s);
+// sg: supergraph variant (pair-table dedupe to one minimum-key edge per
+// pair of trees), else every cross edge is a candidate (hooking variant)
+cudaError_t launch_ins_place(const Dev &d, const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, Index ix,
+                             u64 *ovf, u64 ovf_cap, const int *rep, bool sg, PairTable pt, u64 *ck, int *ca, int *cb,
+                             u64 cand_cap, cudaStream_t s);
+cudaError_t launch_scan_rows(const Dev &d, RowList rl, Ctl *ctl, Csr g, const int *rep, bool sg, PairTable pt,
+                             u64 *ck, int *ca, int *cb, u64 cand_cap, cudaStream_t s);
+cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, bool sg, PairTable pt, u64 *ck,
+                            int *ca, int *cb, u64 cand_cap, cudaStream_t s);
 cudaError_t launch_pairs_compact(const Dev &d, Ctl *ctl, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap,
                                  cudaStream_t s);
 cudaError_t launch_extract(const Dev &d, int n, Csr g, const u64 *ovf, u64 novf_max, Ctl *ctl, int *out,

@@ -46,9 +46,24 @@ def test_grid4096_euler_reversal():
                                  flags=drsf.DETERMINISTIC | drsf.EULER_REVERSAL) == 2
 
 
-def test_rmat22_bench_trajectory():
+@pytest.fixture(scope="module")
+def rmat22():
+    return workloads.rmat_graph(22, 16, seed=5)
+
+
+def test_rmat22_bench_trajectory(rmat22):
     """R-MAT scale 22 (the benchmark workload), the benchmark's own
     trajectory (seed 5): its first 8 steps of one 100K insert batch and one
     100K delete batch."""
-    g = workloads.rmat_graph(22, 16, seed=5)
+    g = rmat22
     assert run_trajectory_pooled(g, [(I, 100_000), (D, 100_000)] * 8, seed=5) == 16
+
+
+@pytest.mark.parametrize("variant", ["sg", "hs"])
+def test_rmat22_replacement_variants(variant, rmat22):
+    """The benchmark trajectory's first two steps with each replacement-edge
+    variant forced (the default picks HS for these inserts and SG for these
+    deletes): same forests as the oracle."""
+    g = rmat22
+    flags = drsf.DETERMINISTIC | (drsf.REPL_SG if variant == "sg" else drsf.REPL_HS)
+    assert run_trajectory_pooled(g, [(I, 100_000), (D, 100_000)] * 2, seed=5, flags=flags) == 4

@@ -217,3 +217,19 @@ def test_validate_flag():
     with pytest.raises(drsf.DRSFError) as e:
         drsf.DynamicForest(g.n, dev_tensor(g.edges()), dev_tensor(bad), flags=drsf.VALIDATE)
     assert e.value.status in (drsf.ENOT_FOREST,)
+
+
+@pytest.mark.parametrize("variant", ["sg", "hs"])
+def test_replacement_edge_variants(variant):
+    """Both replacement-edge variants of Section III, forced for every batch:
+    the supergraph reduction (one minimum-key edge per pair of trees) and
+    hooking on every cross edge give the oracle's forest bit for bit, on
+    inserts and deletes alike."""
+    flags = drsf.DETERMINISTIC | (drsf.REPL_SG if variant == "sg" else drsf.REPL_HS)
+    g = workloads.er_graph(20_000, 25_000, seed=1)
+    st = run_trajectory(g, [(I, 2000), (D, 2000)] * 2, seed=1, flags=flags)
+    assert st["supergraph"] == (1 if variant == "sg" else 0)
+    g = workloads.rmat_graph(16, 16, seed=2)
+    run_trajectory(g, [(I, 1000), (D, 1000), (I, 10_000), (D, 10_000)] * 2, seed=3, flags=flags)
+    g = workloads.grid_graph(512, 512, seed=3)
+    run_trajectory(g, [(D, 5000), (I, 5000)] * 2, seed=4, tree_frac=0.9, local=64, flags=flags)
