@@ -208,6 +208,46 @@ DRSF_API drsf_status drsf_apply(drsf_handle h, drsf_op op, const int32_t *batch,
 DRSF_API drsf_status drsf_apply_host(drsf_handle h, drsf_op op, const int32_t *batch, int64_t len,
                             drsf_stream stream);
 
+/*
+ * drsf_apply_batched -- the batched form: one update of many independent
+ * graphs held by one handle as their disjoint union (not in the paper,
+ * which updates one graph; each graph's update is Algorithm 1).  Graph g
+ * owns vertices [vertex_offsets[g], vertex_offsets[g+1]) and the batch
+ * slice [batch_offsets[g], batch_offsets[g+1]); no edge of G may join two
+ * graphs, and every edge of a slice must have both ends in its graph's
+ * range (else DRSF_EINVAL is latched and the call is skipped, as for an
+ * out-of-range id).  Instead of the grid-wide launch sequence, persistent
+ * kernels keep one group per graph, a thread-block cluster of
+ * cluster_blocks blocks: each group takes the next graph from a
+ * device-side queue (largest work first) and runs that graph's whole
+ * update with cluster barriers only.  Graphs fall into size classes by
+ * vertex count (class c takes graphs with more vertices than class c-1's
+ * max_vertices and at most its own; the last class takes the rest); every
+ * class has its own queue, block size, cluster size and blocks per SM, and
+ * the classes run side by side.  The launch sequence is captured into a
+ * CUDA graph on first use of a shape and replayed.  The result is the same
+ * forest as drsf_apply with the same batch (minimum-key replacement edges,
+ * smallest-root super-roots), and drsf_stats reports the union's counters.
+ *   batch           device, int32[2*len] (ids of the union)
+ *   vertex_offsets  host, int64[num_graphs + 1], non-decreasing, last <= n
+ *   batch_offsets   host, int64[num_graphs + 1], first 0, last len
+ *   classes         host, num_classes (1..4) entries, max_vertices increasing;
+ *                   block_threads 128, 256, 512 or 1024; blocks_per_sm 0 =
+ *                   as many as fit; cluster_blocks 1, 2, 4, 8 or 16
+ * Asynchronous like drsf_apply (the host arrays are copied before return).
+ * Errors: DRSF_EINVAL (arguments), DRSF_ENOMEM, DRSF_ECUDA, DRSF_EPOISONED.
+ */
+typedef struct {
+    int32_t max_vertices;
+    int32_t block_threads;
+    int32_t blocks_per_sm;
+    int32_t cluster_blocks;
+} drsf_batched_class;
+DRSF_API drsf_status drsf_apply_batched(drsf_handle h, drsf_op op, const int32_t *batch, int64_t len,
+                                        int32_t num_graphs, const int64_t *vertex_offsets,
+                                        const int64_t *batch_offsets, const drsf_batched_class *classes,
+                                        int32_t num_classes, drsf_stream stream);
+
 /* drsf_parent -- the output of the D-RSF problem (problem box, Section I):
  * the rooted spanning forest F' of the updated graph G', as parent
  * pointers.  Copies

@@ -56,6 +56,20 @@ class BatchStats(ctypes.Structure):
 NUM_PHASES = 12
 
 
+class BatchedClass(ctypes.Structure):
+    """One size class of drsf_apply_batched: graphs with at most
+    max_vertices vertices (and more than the previous class's), their block
+    size, blocks per SM (0: as many as fit) and blocks per cluster (the
+    group that updates one graph)."""
+    _fields_ = [("max_vertices", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("cluster_blocks", ctypes.c_int32)]
+
+
+# default size classes of the batched form:
+# (max vertices, block threads, blocks per SM, blocks per cluster)
+DEFAULT_CLASSES = ((8192, 256, 0, 1), (65536, 512, 0, 2), (2 ** 31 - 1, 1024, 0, 8))
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("ms", (ctypes.c_double * NUM_PHASES) * 2), ("launches", (ctypes.c_int64 * NUM_PHASES) * 2),
                 ("batches", ctypes.c_int64 * 2)]
@@ -135,6 +149,8 @@ def _load():
         lib.drsf_selftest_barrier_timeout.argtypes = [vp]
         lib.drsf_phase_name.restype = ctypes.c_char_p
         lib.drsf_phase_name.argtypes = [ctypes.c_int]
+        lib.drsf_apply_batched.restype = ctypes.c_int
+        lib.drsf_apply_batched.argtypes = [vp, ctypes.c_int, vp, i64, i32, vp, vp, vp, i32, vp]
         _lib = lib
         return lib
 
@@ -220,6 +236,29 @@ class DynamicForest:
                                   int(t.shape[0]) if t.numel() else 0, _stream_ptr(self._stream))
         if st:
             raise DRSFError(st, "drsf_apply_host")
+
+    def apply_batched(self, op: int, batch: torch.Tensor, vertex_offsets, batch_offsets,
+                      classes=DEFAULT_CLASSES) -> None:
+        """Batched form: the handle holds the disjoint union of independent
+        graphs (graph g owns vertices vertex_offsets[g] .. vertex_offsets[g+1]
+        and batch rows batch_offsets[g] .. batch_offsets[g+1]); persistent
+        per-graph kernels apply every graph's slice.  `classes` is a sequence
+        of (max_vertices, block_threads, blocks_per_sm[, cluster_blocks])
+        size classes."""
+        import numpy as np
+        batch = _dev_i32(batch, "batch", 2)
+        vo = np.ascontiguousarray(vertex_offsets, np.int64)
+        bo = np.ascontiguousarray(batch_offsets, np.int64)
+        if vo.shape != bo.shape or vo.ndim != 1 or len(vo) < 2:
+            raise ValueError("vertex_offsets and batch_offsets must be 1-D of the same length G + 1")
+        rows = [tuple(c) + (1,) * (4 - len(c)) for c in classes]
+        cl = (BatchedClass * len(rows))(*[BatchedClass(*(int(x) for x in r)) for r in rows])
+        st = _lib.drsf_apply_batched(self._h, op, batch.data_ptr() if batch.numel() else None,
+                                     int(batch.shape[0]) if batch.numel() else 0, len(vo) - 1,
+                                     vo.ctypes.data, bo.ctypes.data, ctypes.cast(cl, ctypes.c_void_p),
+                                     len(classes), _stream_ptr(self._stream))
+        if st:
+            raise DRSFError(st, "drsf_apply_batched")
 
     def insert(self, batch: torch.Tensor) -> None:
         self.apply(INSERT, batch)

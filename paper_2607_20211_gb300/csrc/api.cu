@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "kernels.h"
@@ -82,6 +83,21 @@ struct drsf_ctx {
     long long stage_cap = 0;
     cudaEvent_t stage_done = nullptr;
     bool stage_pending = false;
+    // batched form (drsf_apply_batched): persistent per-graph kernels
+    bool b_ready = false;
+    BState *b_state = nullptr;    // device copies of the per-call state and descriptor
+    BDesc *b_desc = nullptr;
+    long long b_gcap = 0;         // graphs the per-graph arrays hold
+    char *b_meta = nullptr;       // device: voff (G+1) | boff (G+1) | order (G)
+    char *b_meta_host = nullptr;  // pinned staging of the same
+    cudaEvent_t b_meta_done = nullptr;
+    bool b_meta_pending = false;
+    cudaStream_t b_cap = nullptr, b_cls[BCLASSES] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t b_fork = nullptr, b_join[BCLASSES] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<std::pair<std::string, cudaGraphExec_t>> b_graphs;   // captured launch sequences
+    BState b_st{};                // scratch pointers (pool, stamps, lists)
+    u64 b_govf_cap = 0;
+    long long b_tile_cap = 0;
     // host-side bounds that decide a storage rebuild without a device read
     long long occ_bound = 0;     // index slots in use (live + deleted)
     long long ovf_bound = 0;     // overflow entries
@@ -481,6 +497,15 @@ static void destroy_all(drsf_ctx *h) {
     if (h->stage_host) cudaFreeHost(h->stage_host);
     if (h->stage_done) cudaEventDestroy(h->stage_done);
     for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+    for (auto &ge : h->b_graphs) cudaGraphExecDestroy(ge.second);
+    if (h->b_meta_host) cudaFreeHost(h->b_meta_host);
+    if (h->b_meta_done) cudaEventDestroy(h->b_meta_done);
+    if (h->b_fork) cudaEventDestroy(h->b_fork);
+    if (h->b_cap) cudaStreamDestroy(h->b_cap);
+    for (int c = 0; c < BCLASSES; ++c) {
+        if (h->b_join[c]) cudaEventDestroy(h->b_join[c]);
+        if (h->b_cls[c]) cudaStreamDestroy(h->b_cls[c]);
+    }
     delete h;
 }
 
@@ -746,6 +771,237 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
     prof_begin(h, PH_REVERSE, s);
     CK(launch_reverse(h->dev, ctl, h->act, h->pold, h->mark, h->chx, h->chy, h->parent, euler ? 0 : 1, s));
     prof_end(h, PH_REVERSE, 1, s);
+    return DRSF_OK;
+}
+
+// ------------------------------------------------------- batched form
+
+// Scratch of the persistent per-graph kernels, allocated on first use.
+static drsf_status batched_scratch(drsf_ctx *h, cudaStream_t s) {
+    if (h->b_ready) return DRSF_OK;
+    const size_t n = (size_t)h->n;
+    BState &b = h->b_st;
+    int **iv[] = {&b.J, &b.R, &b.A, &b.Dv, &b.roff, &b.comp, &b.minp, &b.pidx, &b.plist, &b.pdeg, &b.poff, &b.pcur,
+                  &b.newroot, &b.flist, &b.chx, &b.chy};
+    for (int **p : iv) CKA(halloc(h, p, n + 1, s));
+    CKA(halloc(h, &b.adj, 2 * n + 2, s));
+    unsigned **st[] = {&b.st_aff, &b.st_cut, &b.st_piece, &b.st_vis, &b.st_rr};
+    for (unsigned **p : st) {
+        CKA(halloc(h, p, n + 1, s));
+        CK(cudaMemsetAsync(*p, 0, (n + 1) * sizeof(unsigned), s));
+    }
+    CKA(halloc(h, &b.best, n + 1, s));
+    CKA(halloc(h, &b.er, n + 1, s));
+    CKA(halloc(h, &b.pool_ctr, 1, s));
+    CKA(halloc(h, &b.qctr, BCLASSES, s));
+    CKA(halloc(h, &h->b_state, 1, s));
+    CKA(halloc(h, &h->b_desc, 1, s));
+    CK(cudaStreamCreateWithFlags(&h->b_cap, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->b_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->b_meta_done, cudaEventDisableTiming));
+    for (int c = 0; c < BCLASSES; ++c) {
+        CK(cudaStreamCreateWithFlags(&h->b_cls[c], cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->b_join[c], cudaEventDisableTiming));
+    }
+    h->b_ready = true;
+    return DRSF_OK;
+}
+
+// Per-graph arrays for G graphs and the candidate pool for this call.
+static drsf_status batched_capacity(drsf_ctx *h, long long G, long long len, cudaStream_t s) {
+    BState &b = h->b_st;
+    if (G > h->b_gcap) {
+        CK(cudaStreamSynchronize(s));
+        if (h->b_meta_host) cudaFreeHost(h->b_meta_host);
+        h->b_meta_host = nullptr;
+        hfree(h, &h->b_meta, s);
+        hfree(h, &b.gcnt, s);
+        hfree(h, &b.gcur, s);
+        hfree(h, &b.govf_start, s);
+        long long cap = std::max<long long>(G, 256);
+        size_t bytes = (size_t)(2 * (cap + 1)) * sizeof(long long) + (size_t)cap * sizeof(int);
+        CKA(halloc(h, &h->b_meta, bytes, s));
+        CK(cudaMallocHost((void **)&h->b_meta_host, bytes));
+        CKA(halloc(h, &b.gcnt, (size_t)cap + 1, s));
+        CKA(halloc(h, &b.gcur, (size_t)cap + 1, s));
+        CKA(halloc(h, &b.govf_start, (size_t)cap + 1, s));
+        h->b_gcap = cap;
+        h->b_meta_pending = false;
+    }
+    // candidates: at most the batch (insert) or every live edge (delete),
+    // plus one partly used chunk per graph
+    const u64 need = (u64)std::max<long long>(len, h->col_cap / 2 + (long long)h->ovf_cap) + (u64)(G + 1) * 2048u;
+    if (need > b.pool_cap) {
+        CK(cudaStreamSynchronize(s));
+        hfree(h, &b.pk, s);
+        hfree(h, &b.pa, s);
+        hfree(h, &b.pb, s);
+        CKA(halloc(h, &b.pk, need, s));
+        CKA(halloc(h, &b.pa, need, s));
+        CKA(halloc(h, &b.pb, need, s));
+        b.pool_cap = need;
+    }
+    // tiles of the scanned rows: graph g's start at off[first vertex] / 32 + g
+    const long long ntile = h->col_cap / 32 + G + 2;
+    if (ntile > h->b_tile_cap) {
+        CK(cudaStreamSynchronize(s));
+        hfree(h, &b.tile, s);
+        CKA(halloc(h, &b.tile, (size_t)ntile, s));
+        h->b_tile_cap = ntile;
+    }
+    // overflow buckets: as large as the overflow list (which a rebuild resizes)
+    if (!b.govf || h->b_govf_cap < h->ovf_cap) {
+        CK(cudaStreamSynchronize(s));
+        hfree(h, &b.govf, s);
+        CKA(halloc(h, &b.govf, (size_t)h->ovf_cap, s));
+        h->b_govf_cap = h->ovf_cap;
+    }
+    return DRSF_OK;
+}
+
+drsf_status drsf_apply_batched(drsf_handle h, drsf_op op, const int32_t *batch, int64_t len, int32_t num_graphs,
+                               const int64_t *vertex_offsets, const int64_t *batch_offsets,
+                               const drsf_batched_class *classes, int32_t num_classes, drsf_stream stream) {
+    if (!h || (op != DRSF_INSERT && op != DRSF_DELETE) || len < 0 || (len > 0 && !batch) || num_graphs < 1 ||
+        !vertex_offsets || !batch_offsets || !classes || num_classes < 1 || num_classes > BCLASSES)
+        return DRSF_EINVAL;
+    if (h->poisoned) return DRSF_EPOISONED;
+    if (len > (int64_t)1 << 31) return DRSF_EINVAL;
+    const long long G = num_graphs;
+    if (vertex_offsets[0] < 0 || vertex_offsets[G] > h->n || batch_offsets[0] != 0 || batch_offsets[G] != len)
+        return DRSF_EINVAL;
+    for (long long g = 0; g < G; ++g)
+        if (vertex_offsets[g + 1] < vertex_offsets[g] || batch_offsets[g + 1] < batch_offsets[g]) return DRSF_EINVAL;
+    for (int c = 0; c < num_classes; ++c) {
+        const int t = classes[c].block_threads, cb = classes[c].cluster_blocks;
+        if ((t != 128 && t != 256 && t != 512 && t != 1024) || classes[c].blocks_per_sm < 0) return DRSF_EINVAL;
+        if (cb != 1 && cb != 2 && cb != 4 && cb != 8 && cb != 16) return DRSF_EINVAL;
+        if (c > 0 && classes[c].max_vertices <= classes[c - 1].max_vertices) return DRSF_EINVAL;
+    }
+    set_dev(h);
+    cudaStream_t s = (cudaStream_t)stream;
+    drsf_status st = ensure_batch(h, len, s);
+    if (st) return st;
+    st = storage_check(h, op, len, s);
+    if (st) return st;
+    st = batched_scratch(h, s);
+    if (st) return st;
+    st = batched_capacity(h, G, len, s);
+    if (st) return st;
+    BState &b = h->b_st;
+    // queue order: size class by vertex count, then the largest work first
+    // (batch edges + vertices) so the long graphs start early
+    std::vector<std::vector<int>> per(num_classes);
+    for (long long g = 0; g < G; ++g) {
+        const long long nv = vertex_offsets[g + 1] - vertex_offsets[g];
+        int c = 0;
+        while (c < num_classes - 1 && nv > classes[c].max_vertices) ++c;
+        per[c].push_back((int)g);
+    }
+    char *mh = h->b_meta_host;
+    if (h->b_meta_pending) CK(cudaEventSynchronize(h->b_meta_done));
+    long long *voff_h = (long long *)mh, *boff_h = voff_h + (G + 1);
+    int *order_h = (int *)(boff_h + (G + 1));
+    memcpy(voff_h, vertex_offsets, (size_t)(G + 1) * sizeof(long long));
+    memcpy(boff_h, batch_offsets, (size_t)(G + 1) * sizeof(long long));
+    int q[BCLASSES + 1] = {0};
+    long long pos = 0;
+    for (int c = 0; c < num_classes; ++c) {
+        auto &v = per[c];
+        std::stable_sort(v.begin(), v.end(), [&](int x, int y) {
+            long long wx = (batch_offsets[x + 1] - batch_offsets[x]) + (vertex_offsets[x + 1] - vertex_offsets[x]);
+            long long wy = (batch_offsets[y + 1] - batch_offsets[y]) + (vertex_offsets[y + 1] - vertex_offsets[y]);
+            return wx > wy;
+        });
+        q[c] = (int)pos;
+        for (int g : v) order_h[pos++] = g;
+    }
+    q[num_classes] = (int)pos;
+    const size_t mbytes = (size_t)(2 * (G + 1)) * sizeof(long long) + (size_t)G * sizeof(int);
+    long long *voff_d = (long long *)h->b_meta, *boff_d = voff_d + (G + 1);
+    int *order_d = (int *)(boff_d + (G + 1));
+    CK(cudaMemcpyAsync(h->b_meta, mh, mbytes, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(h->b_meta_done, s));
+    h->b_meta_pending = true;
+    // the per-call state: current storage pointers + scratch
+    b.ctl = h->ctl;
+    b.parent = h->parent;
+    b.rep = h->rep;
+    b.g = Csr{h->off, h->used, h->col};
+    b.ix = h->ix;
+    b.ovf = h->ovf;
+    b.ovf_cap = h->ovf_cap;
+    b.nkey = h->nkey;
+    b.nslot = h->nslot;
+    b.pt_pk = h->pt.pk;
+    b.pt_mk = h->pt.mk;
+    b.pt_mask = h->pt.mask;
+    b.desc = h->b_desc;
+    BDesc d{};
+    d.batch = batch;
+    d.len = len;
+    d.voff = voff_d;
+    d.boff = boff_d;
+    d.order = order_d;
+    d.G = (int)G;
+    d.op = (int)op;
+    CK(launch_bset(h->b_state, b, h->b_desc, d, s));
+    // one captured launch sequence per (op, class queues, launch shapes)
+    std::string key = std::to_string((int)op);
+    // the classes run side by side, each on a share of the GPU in
+    // proportion to its vertices (a class's grid alone would fill the GPU
+    // and the classes would then run one after another)
+    double vsum[BCLASSES] = {0}, vtot = 0;
+    for (int c = 0; c < num_classes; ++c) {
+        for (int g : per[c]) vsum[c] += (double)(vertex_offsets[g + 1] - vertex_offsets[g]) + 1.0;
+        vtot += vsum[c];
+    }
+    unsigned grid[BCLASSES] = {0};
+    for (int c = 0; c < num_classes; ++c) {
+        const unsigned cb = (unsigned)classes[c].cluster_blocks;
+        grid[c] = bpersist_grid(h->dev.nsm, classes[c].block_threads, classes[c].blocks_per_sm,
+                                classes[c].cluster_blocks);
+        if (vtot > 0 && vsum[c] < vtot) {
+            unsigned share = (unsigned)((double)(grid[c] / cb) * vsum[c] / vtot) * cb;
+            grid[c] = share < cb ? cb : share;
+        }
+        key += "|" + std::to_string(q[c]) + ":" + std::to_string(q[c + 1]) + ":" +
+               std::to_string(classes[c].block_threads) + ":" + std::to_string(grid[c]) + ":" +
+               std::to_string(classes[c].cluster_blocks);
+    }
+    cudaGraphExec_t exec = nullptr;
+    for (auto &ge : h->b_graphs)
+        if (ge.first == key) exec = ge.second;
+    if (!exec) {
+        CK(cudaStreamBeginCapture(h->b_cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = launch_bprologue(h->dev, h->b_state, h->b_cap);
+        if (e == cudaSuccess) e = cudaEventRecord(h->b_fork, h->b_cap);
+        for (int c = 0; c < num_classes && e == cudaSuccess; ++c) {
+            if (q[c + 1] == q[c]) continue;
+            e = cudaStreamWaitEvent(h->b_cls[c], h->b_fork, 0);
+            if (e == cudaSuccess)
+                e = launch_bpersist(h->b_state, c, q[c], q[c + 1], classes[c].block_threads, grid[c],
+                                    classes[c].cluster_blocks, h->b_cls[c]);
+            if (e == cudaSuccess) e = cudaEventRecord(h->b_join[c], h->b_cls[c]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->b_cap, h->b_join[c], 0);
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(h->b_cap, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return DRSF_ECUDA;
+        }
+        if (h->b_graphs.size() >= 8) {
+            cudaGraphExecDestroy(h->b_graphs.front().second);
+            h->b_graphs.erase(h->b_graphs.begin());
+        }
+        h->b_graphs.emplace_back(key, exec);
+    }
+    CK(cudaGraphLaunch(exec, s));
+    h->last_sg = 0;
     return DRSF_OK;
 }
 

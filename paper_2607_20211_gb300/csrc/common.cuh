@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <climits>
+
 #include "../../include/drsf.h"
 
 typedef unsigned long long u64;
@@ -105,6 +107,36 @@ __device__ __forceinline__ u64 hslot(u64 k, u64 mask) {
     return k & mask;
 }
 
+// Edge index probes (open addressing, linear probing).
+// Insert-if-absent.  Returns the slot when this call claimed it, -1-slot
+// when the key was already present, LLONG_MIN when the table is full.
+__device__ __forceinline__ long long index_claim(Index ix, u64 key) {
+    u64 s = hslot(key, ix.mask);
+    for (u64 p = 0; p <= ix.mask; ++p) {
+        u64 cur = __ldcg(&ix.key[s]);
+        if (cur == key) return -1 - (long long)s;
+        if (cur == EMPTY_KEY) {
+            u64 old = atomicCAS(&ix.key[s], EMPTY_KEY, key);
+            if (old == EMPTY_KEY) return (long long)s;
+            if (old == key) return -1 - (long long)s;
+        }
+        s = (s + 1) & ix.mask;
+    }
+    return LLONG_MIN;
+}
+
+// Lookup; -1 when absent.  Deleted entries (TOMB_KEY) are probed past.
+__device__ __forceinline__ long long index_find(Index ix, u64 key) {
+    u64 s = hslot(key, ix.mask);
+    for (u64 p = 0; p <= ix.mask; ++p) {
+        u64 cur = __ldcg(&ix.key[s]);
+        if (cur == key) return (long long)s;
+        if (cur == EMPTY_KEY) return -1;
+        s = (s + 1) & ix.mask;
+    }
+    return -1;
+}
+
 // Warp-aggregated append: one atomicAdd per warp; returns the slot of this
 // lane (or -1 when pred is false).
 __device__ __forceinline__ long long agg_append(u64 *ctr, bool pred) {
@@ -117,6 +149,17 @@ __device__ __forceinline__ long long agg_append(u64 *ctr, bool pred) {
     if (lane == leader) base = atomicAdd(ctr, (u64)__popc(m));
     base = __shfl_sync(m, base, leader);
     return (long long)(base + __popc(m & ((1u << lane) - 1u)));
+}
+
+// One slot of row r's append cursor per calling lane; lanes of a warp with
+// the same row share one atomicAdd.
+__device__ __forceinline__ int row_slot(int *used, int r) {
+    const unsigned grp = __match_any_sync(__activemask(), r);
+    const int lane = threadIdx.x & 31, ld = __ffs(grp) - 1;
+    int base = 0;
+    if (lane == ld) base = atomicAdd(&used[r], __popc(grp));
+    base = __shfl_sync(grp, base, ld);
+    return base + __popc(grp & ((1u << lane) - 1u));
 }
 
 // Pair table: piece pair (min, max) -> minimum edge key between the two

@@ -17,35 +17,6 @@ __device__ __forceinline__ void agg_count(long long *ctr, bool pred, long long s
         atomicAdd((u64 *)ctr, (u64)(sign * (long long)__popc(m)));
 }
 
-// Insert-if-absent.  Returns the slot when this call claimed it, -1-slot
-// when the key was already present, LLONG_MIN when the table is full.
-__device__ long long index_claim(Index ix, u64 key) {
-    u64 s = hslot(key, ix.mask);
-    for (u64 p = 0; p <= ix.mask; ++p) {
-        u64 cur = __ldcg(&ix.key[s]);
-        if (cur == key) return -1 - (long long)s;
-        if (cur == EMPTY_KEY) {
-            u64 old = atomicCAS(&ix.key[s], EMPTY_KEY, key);
-            if (old == EMPTY_KEY) return (long long)s;
-            if (old == key) return -1 - (long long)s;
-        }
-        s = (s + 1) & ix.mask;
-    }
-    return LLONG_MIN;
-}
-
-// Lookup; -1 when absent.  Deleted entries (TOMB_KEY) are probed past.
-__device__ long long index_find(Index ix, u64 key) {
-    u64 s = hslot(key, ix.mask);
-    for (u64 p = 0; p <= ix.mask; ++p) {
-        u64 cur = __ldcg(&ix.key[s]);
-        if (cur == key) return (long long)s;
-        if (cur == EMPTY_KEY) return -1;
-        s = (s + 1) & ix.mask;
-    }
-    return -1;
-}
-
 // ------------------------------------------------------------------ build
 
 __global__ void k_check_range(const int *a, long long cnt, int n, int *bad) {
@@ -221,17 +192,6 @@ __global__ void k_ins_claim(const int *batch, long long len, Index ix, Ctl *ctl,
     }
     block_add(&ctl->self_loops, loops);
     block_add(&ctl->dropped, drops);
-}
-
-// One slot of row r's append cursor per calling lane; lanes of a warp with
-// the same row share one atomicAdd.
-__device__ __forceinline__ int row_slot(int *used, int r) {
-    const unsigned grp = __match_any_sync(__activemask(), r);
-    const int lane = threadIdx.x & 31, ld = __ffs(grp) - 1;
-    int base = 0;
-    if (lane == ld) base = atomicAdd(&used[r], __popc(grp));
-    base = __shfl_sync(grp, base, ld);
-    return base + __popc(grp & ((1u << lane) - 1u));
 }
 
 // Insert, step 2: append each new edge to both CSR rows (warp-aggregated

@@ -129,3 +129,47 @@ struct EtArgs {
 };
 cudaError_t launch_et_marks(const Dev &d, Ctl *ctl, EtArgs a, cudaStream_t s);
 unsigned coop_blocks_et(int nsm);
+// batched.cu -----------------------------------------------------------
+// Persistent per-graph kernels over the disjoint union of many graphs.
+#define BCLASSES 4
+struct BDesc {               // per call
+    const int *batch;        // union batch (ids offset per graph)
+    long long len;
+    const long long *voff;   // G + 1 vertex offsets
+    const long long *boff;   // G + 1 batch offsets
+    const int *order;        // graphs in queue order, class by class
+    int G;
+    int op;
+};
+struct BState {              // device pointers of one handle (per call)
+    Ctl *ctl;
+    int *parent, *rep;
+    Csr g;
+    Index ix;
+    u64 *ovf;
+    u64 ovf_cap;
+    u64 *nkey, *nslot;       // batch-indexed
+    // vertex-indexed scratch (graph g uses its own vertex range)
+    int *J, *R, *A, *Dv, *roff, *comp, *minp, *pidx, *plist, *pdeg, *poff, *pcur, *newroot, *flist, *chx, *chy;
+    int *adj;                // 2 per vertex
+    int *tile;               // row of the first entry of each 32-entry tile of a graph's scanned rows
+    unsigned *st_aff, *st_cut, *st_piece, *st_vis, *st_rr;   // epoch stamps
+    u64 *best, *er;
+    // candidate pool, handed out in chunks
+    u64 *pk;
+    int *pa, *pb;
+    u64 pool_cap;
+    u64 *pool_ctr;
+    u64 *pt_pk, *pt_mk;      // pair table (shared with the grid path; empty between calls)
+    u64 pt_mask;
+    unsigned *qctr;          // queue counter per class
+    int *gcnt, *gcur;        // overflow edges per graph
+    long long *govf_start;
+    u64 *govf;               // positions in ovf, grouped by graph
+    BDesc *desc;
+};
+cudaError_t launch_bset(BState *dst_state, const BState &st, BDesc *dst_desc, const BDesc &d, cudaStream_t s);
+cudaError_t launch_bprologue(const Dev &dv, const BState *S, cudaStream_t s);
+unsigned bpersist_grid(int nsm, int threads, int per_sm, int cluster);
+cudaError_t launch_bpersist(const BState *S, int cls, int q_lo, int q_hi, int threads, unsigned grid, int cluster,
+                            cudaStream_t s);
