@@ -57,12 +57,25 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--euler", action="store_true", help="Euler-tour path marks (Algorithm 3)")
+    p.add_argument("--sweep", default="", help="comma-separated batch sizes: one JSON line per size")
+    p.add_argument("--no-variants", action="store_true", help="skip the SG / HS replacement-variant timing")
     return p.parse_args()
 
 
 # ------------------------------------------------------------ workloads
 
+_GRAPHS = {}
+
+
 def make_graph(name):
+    """The workload's graph and trajectory parameters (generated once per
+    process)."""
+    if name not in _GRAPHS:
+        _GRAPHS[name] = _make_graph(name)
+    return _GRAPHS[name]
+
+
+def _make_graph(name):
     import workloads
     if name == "rmat22":
         return workloads.rmat_graph(22, 16, seed=5), dict(tree_frac=0.5, local=0, batch=100_000)
@@ -280,7 +293,6 @@ def run_ours(args, rank, ws, local):
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
-    f.profile_start(2 * K + 4)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     barrier()
     torch.cuda.synchronize()
@@ -293,8 +305,25 @@ def run_ours(args, rank, ws, local):
         ev[k][2].record(stream)
     torch.cuda.synchronize()
     barrier()
-    prof = f.profile_stop()
     final = f.parent().cpu().numpy()
+    f.close()
+    # per-phase device times: the same W + K steps replayed on a fresh
+    # handle with every phase bracketed by CUDA events (direct launches:
+    # events cannot sit between the kernels of a captured graph)
+    f = drsf.DynamicForest(g.n, edges_d, parent_d, flags=flags)
+    for s in range(W):
+        for op in (0, 1):
+            f.apply(op, dev_batches[s][op])
+    torch.cuda.synchronize()
+    f.profile_start(2 * K + 4)
+    for k in range(K):
+        flush.zero_()
+        f.apply(0, dev_batches[W + k][0])
+        f.apply(1, dev_batches[W + k][1])
+    torch.cuda.synchronize()
+    prof = f.profile_stop()
+    if not np.array_equal(f.parent().cpu().numpy(), final_plan):
+        raise RuntimeError("profiled replay diverged from the planning pass")
     # static rebuild of the final graph from scratch (the plain alternative)
     st_ms = []
     levels = 0
@@ -309,7 +338,8 @@ def run_ours(args, rank, ws, local):
     f.close()
     if not np.array_equal(final, final_plan):
         raise RuntimeError("timed replay diverged from the planning pass")
-    variants = replacement_variants(g, edges_d, parent_d, dev_batches, W, min(K, 5), flush, stream)
+    variants = None if args.no_variants else replacement_variants(g, edges_d, parent_d, dev_batches, W, min(K, 5),
+                                                                   flush, stream)
     ins_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
     del_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
     step_ms = [i + d for i, d in zip(ins_ms, del_ms)]
@@ -341,6 +371,8 @@ def run_ours(args, rank, ws, local):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "phase_timing": "CUDA events around each phase over the same K steps, replayed on a fresh handle "
+                                "with direct launches (the timed run replays captured CUDA graphs)",
                 "frac": round(achieved / peak, 4), "traffic": ncu_traffic(dom),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "algorithmic_bytes_per_launch": int(per_launch_bytes),
@@ -765,6 +797,11 @@ def main():
         run_batched(args, rank, ws, local)
     elif args.workload == "serving":
         run_serving(args, rank, ws, local)
+    elif args.sweep:
+        # batch-size sweep on one workload (latency per batch as b changes)
+        for b in [int(x) for x in args.sweep.split(",") if x]:
+            args.batch = b
+            run_ours(args, rank, ws, local)
     else:
         run_ours(args, rank, ws, local)
     import torch.distributed as dist

@@ -36,6 +36,12 @@ struct drsf_ctx {
     int jump_sync = 2;   // root search: 2 asynchronous doubling, 1 synchronous rounds, 0 path halving
     int pending_einval = 0;
     int last_sg = 0;     // the last batch took the supergraph variant
+    // captured per-batch launch sequences (CUDA graphs), valid for storage
+    // generation u_gen; gen moves whenever a storage or batch buffer moves
+    std::vector<std::pair<std::string, cudaGraphExec_t>> u_graphs;
+    long long gen = 0, u_gen = 0;
+    bool graphs_ok = true;
+    cudaStream_t u_cap = nullptr;
 
     Ctl *ctl = nullptr;
     Ctl *ctl_host = nullptr;   // pinned
@@ -309,6 +315,7 @@ static drsf_status build_graph(drsf_ctx *h, const int *edges, long long m, cudaS
     h->occ_bound = m2;
     h->ovf_bound = 0;
     h->ctomb_bound = 0;
+    h->gen++;   // captured launch sequences point into the old storage
     *m_out = m2;
     if (self_loops_out) *self_loops_out = (long long)hc[1];
     return DRSF_OK;
@@ -335,6 +342,7 @@ static drsf_status ensure_batch(drsf_ctx *h, long long len, cudaStream_t s) {
     CK(cudaMemsetAsync(h->pt.mk, 0xFF, T * sizeof(u64), s));
     h->pt.mask = T - 1;
     h->batch_cap = cap;
+    h->gen++;
     return DRSF_OK;
 }
 
@@ -498,6 +506,8 @@ static void destroy_all(drsf_ctx *h) {
     if (h->stage_done) cudaEventDestroy(h->stage_done);
     for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
     for (auto &ge : h->b_graphs) cudaGraphExecDestroy(ge.second);
+    for (auto &ge : h->u_graphs) cudaGraphExecDestroy(ge.second);
+    if (h->u_cap) cudaStreamDestroy(h->u_cap);
     if (h->b_meta_host) cudaFreeHost(h->b_meta_host);
     if (h->b_meta_done) cudaEventDestroy(h->b_meta_done);
     if (h->b_fork) cudaEventDestroy(h->b_fork);
@@ -615,6 +625,10 @@ drsf_status drsf_create(int32_t n, const int32_t *edges, int64_t m, const int32_
     // DRSF_JUMP=halving the in-place path-halving walks
     const char *jm = getenv("DRSF_JUMP");
     h->jump_sync = jm && strcmp(jm, "halving") == 0 ? 0 : (jm && strcmp(jm, "sync") == 0 ? 1 : 2);
+    // DRSF_GRAPHS=0: launch every batch's kernels one by one instead of
+    // replaying a captured CUDA graph
+    const char *gr = getenv("DRSF_GRAPHS");
+    h->graphs_ok = !(gr && strcmp(gr, "0") == 0);
     drsf_status st = create_impl(h, edges, m, parent, s);
     if (st != DRSF_OK) {
         destroy_all(h);
@@ -639,29 +653,21 @@ static bool use_supergraph(const drsf_ctx *h, int op, long long len) {
     return keys > (long long)h->n / 16;
 }
 
-static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t len, cudaStream_t s) {
-    drsf_status st = ensure_batch(h, len, s);
-    if (st) return st;
-    st = storage_check(h, op, len, s);
-    if (st) return st;
-    const bool sg = use_supergraph(h, op, len);
-    h->last_sg = sg ? 1 : 0;
+// The launch sequence of one batch after k_begin (Algorithm 1).  Its
+// launches depend on the handle's storage, the operation, the
+// replacement-edge variant and, for the batch kernels' grids, `glen`; the
+// batch itself is read from the control block, so one captured copy of the
+// sequence serves every batch with the same key.
+static drsf_status launch_rest(drsf_ctx *h, int op, bool sg, long long glen, cudaStream_t s) {
     Ctl *ctl = h->ctl;
     Csr g{h->off, h->used, h->col};
-    if (h->prof_on) {
-        h->prof_batches++;
-        h->prof_op = op;
-        h->prof_nb[op]++;
-    }
-    prof_begin(h, PH_BEGIN, s);
-    CK(launch_begin(ctl, op, len, s));
-    CK(launch_validate_batch(batch, len, h->n, ctl, s));
-    prof_end(h, PH_BEGIN, len > 0 ? 2 : 1, s);
+    CK(launch_validate_batch(glen, h->n, ctl, s));
+    prof_end(h, PH_BEGIN, 2, s);
     if (op == DRSF_INSERT) {
         // Algorithm 1, insert: F^ = F, M = B; rep of the previous batch is current
         prof_begin(h, PH_INS_CLAIM, s);
-        CK(launch_ins_claim(batch, len, h->ix, ctl, h->nkey, h->nslot, s));
-        prof_end(h, PH_INS_CLAIM, len > 0 ? 1 : 0, s);
+        CK(launch_ins_claim(glen, h->ix, ctl, h->nkey, h->nslot, s));
+        prof_end(h, PH_INS_CLAIM, 1, s);
         prof_begin(h, PH_INS_PLACE, s);
         CK(launch_ins_place(h->dev, h->nkey, h->nslot, ctl, g, h->ix, h->ovf, h->ovf_cap, h->rep, sg, h->pt,
                             h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
@@ -670,9 +676,9 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
     } else {
         // Algorithm 1, delete: remove B, cut tree edges, re-label the cut trees
         prof_begin(h, PH_DEL_CLAIM, s);
-        CK(launch_del_claim(batch, len, h->ix, g, h->ovf, h->parent, h->rep, ctl, h->aff_ep, h->cut_ep,
-                            h->cutlist, h->wgt, s));
-        prof_end(h, PH_DEL_CLAIM, len > 0 ? 1 : 0, s);
+        CK(launch_del_claim(glen, h->ix, g, h->ovf, h->parent, h->rep, ctl, h->aff_ep, h->cut_ep, h->cutlist,
+                            h->wgt, s));
+        prof_end(h, PH_DEL_CLAIM, 1, s);
         prof_begin(h, PH_AFF, s);
         CK(launch_aff_collect(h->dev, h->n, h->rep, h->aff_ep, h->A, h->rold, h->wgt, h->heavy, ctl, h->parent,
                               h->jump_sync == 2 ? h->J0 : nullptr, s));
@@ -771,6 +777,67 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
     prof_begin(h, PH_REVERSE, s);
     CK(launch_reverse(h->dev, ctl, h->act, h->pold, h->mark, h->chx, h->chy, h->parent, euler ? 0 : 1, s));
     prof_end(h, PH_REVERSE, 1, s);
+    return DRSF_OK;
+}
+
+// Forget the captured launch sequences (the storage they point into moved).
+static void drop_graphs(drsf_ctx *h) {
+    for (auto &ge : h->u_graphs) cudaGraphExecDestroy(ge.second);
+    h->u_graphs.clear();
+}
+
+static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t len, cudaStream_t s) {
+    drsf_status st = ensure_batch(h, len, s);
+    if (st) return st;
+    st = storage_check(h, op, len, s);
+    if (st) return st;
+    const bool sg = use_supergraph(h, op, len);
+    h->last_sg = sg ? 1 : 0;
+    if (h->prof_on) {
+        h->prof_batches++;
+        h->prof_op = op;
+        h->prof_nb[op]++;
+    }
+    prof_begin(h, PH_BEGIN, s);
+    CK(launch_begin(h->ctl, op, len, batch, s));
+    // per-phase profiling brackets the phases with events: launch directly
+    if (h->prof_on || !h->graphs_ok) return launch_rest(h, op, sg, len, s);
+    // otherwise replay the captured sequence for this (storage, op, variant,
+    // grid size class of the batch kernels); capture it on first use
+    long long glen = 4096;
+    while (glen < len) glen <<= 2;
+    if (h->u_gen != h->gen) {
+        drop_graphs(h);
+        h->u_gen = h->gen;
+    }
+    const std::string key = std::to_string(op) + ":" + std::to_string(sg ? 1 : 0) + ":" + std::to_string(glen);
+    cudaGraphExec_t exec = nullptr;
+    for (auto &ge : h->u_graphs)
+        if (ge.first == key) exec = ge.second;
+    if (!exec) {
+        // recorded on a stream of the library's own (the caller's stream may
+        // be the legacy default stream, which cannot be captured); nothing
+        // runs while recording, the replay below is ordered on s
+        if (!h->u_cap) CK(cudaStreamCreateWithFlags(&h->u_cap, cudaStreamNonBlocking));
+        CK(cudaStreamBeginCapture(h->u_cap, cudaStreamCaptureModeThreadLocal));
+        drsf_status rs = launch_rest(h, op, sg, glen, h->u_cap);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->u_cap, &graph);
+        if (rs == DRSF_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (rs != DRSF_OK || e != cudaSuccess || !exec) {
+            // capture not possible here: launch directly from now on
+            cudaGetLastError();
+            h->graphs_ok = false;
+            return launch_rest(h, op, sg, len, s);
+        }
+        if (h->u_graphs.size() >= 16) {
+            cudaGraphExecDestroy(h->u_graphs.front().second);
+            h->u_graphs.erase(h->u_graphs.begin());
+        }
+        h->u_graphs.emplace_back(key, exec);
+    }
+    CK(cudaGraphLaunch(exec, s));
     return DRSF_OK;
 }
 

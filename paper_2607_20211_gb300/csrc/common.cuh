@@ -74,6 +74,7 @@ struct Ctl {
     long long reversed;
     long long batch_len;
     long long overflow_total;
+    const int *batch;       // the current batch (device), set by k_begin
 };
 
 // The edge index.

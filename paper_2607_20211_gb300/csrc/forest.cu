@@ -60,9 +60,12 @@ __device__ __forceinline__ void load_ipt(const int *a, long long i0, long long c
 __device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ long long gstride() { return (long long)gridDim.x * blockDim.x; }
 
-// Reset the per-batch counters and advance the epoch.
-__global__ void k_begin(Ctl *ctl, int op, long long len) {
+// Reset the per-batch counters, advance the epoch and record the batch (the
+// kernels after this one read the batch and its length from the control
+// block, so their launches do not depend on them).
+__global__ void k_begin(Ctl *ctl, int op, long long len, const int *batch) {
     if (threadIdx.x != 0) return;
+    ctl->batch = batch;
     ctl->epoch += 1;
     ctl->skip = 0;
     ctl->op = op;
@@ -1140,8 +1143,8 @@ unsigned coop_blocks_orient(int nsm) {
 }
 unsigned coop_blocks_mark(int nsm) { return coop_blocks((const void *)k_mark, nsm, 4); }
 
-cudaError_t launch_begin(Ctl *ctl, int op, long long len, cudaStream_t s) {
-    k_begin<<<1, 32, 0, s>>>(ctl, op, len);
+cudaError_t launch_begin(Ctl *ctl, int op, long long len, const int *batch, cudaStream_t s) {
+    k_begin<<<1, 32, 0, s>>>(ctl, op, len, batch);
     return cudaGetLastError();
 }
 cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, int *A, int *rold,

@@ -150,7 +150,9 @@ __global__ void k_fill(const u64 *dkey, const u64 *dslot, long long m, Csr g, In
 
 // ------------------------------------------------------------ per batch
 
-__global__ void k_validate_batch(const int *batch, long long len, int n, Ctl *ctl) {
+__global__ void k_validate_batch(int n, Ctl *ctl) {
+    const int *batch = ctl->batch;
+    const long long len = ctl->batch_len;
     GS_LOOP(i, 2 * len) {
         int x = batch[i];
         if (x < 0 || x >= n) {
@@ -162,8 +164,10 @@ __global__ void k_validate_batch(const int *batch, long long len, int n, Ctl *ct
 
 // Insert, step 1 (batch normalisation): drop self-loops, repeated pairs and
 // edges already in G; claim an index slot for each new edge.
-__global__ void k_ins_claim(const int *batch, long long len, Index ix, Ctl *ctl, u64 *nkey, u64 *nslot) {
+__global__ void k_ins_claim(Index ix, Ctl *ctl, u64 *nkey, u64 *nslot) {
     if (*(volatile int *)&ctl->skip) return;
+    const int *batch = ctl->batch;
+    const long long len = ctl->batch_len;
     // block-uniform loop: counters and the list append are aggregated per
     // block (one atomic per block instead of one per warp)
     long long loops = 0, drops = 0;
@@ -265,10 +269,11 @@ __global__ void k_ins_place(const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, 
 // deleted edge {u, v} with parent[u] == v, parent[u] <- u (either
 // orientation).  The old root of a cut tree is stamped "affected"; the cut
 // vertex becomes a piece root and is stamped in cut_ep.
-__global__ void k_del_claim(const int *batch, long long len, Index ix, Csr g, u64 *ovf, int *parent,
-                            const int *rep, Ctl *ctl, unsigned *aff_ep, unsigned *cut_ep, int *cutlist,
-                            unsigned *w) {
+__global__ void k_del_claim(Index ix, Csr g, u64 *ovf, int *parent, const int *rep, Ctl *ctl, unsigned *aff_ep,
+                            unsigned *cut_ep, int *cutlist, unsigned *w) {
     if (*(volatile int *)&ctl->skip) return;
+    const int *batch = ctl->batch;
+    const long long len = ctl->batch_len;
     unsigned ep = ctl->epoch;
     // block-uniform loop: counters and the cut list append are aggregated
     // per block (one atomic per block instead of one per warp)
@@ -614,15 +619,14 @@ cudaError_t launch_fill(const u64 *dkey, const u64 *dslot, long long m, Csr g, I
     k_fill<<<gsz(m), BLK, 0, s>>>(dkey, dslot, m, g, ix);
     return cudaGetLastError();
 }
-cudaError_t launch_validate_batch(const int *batch, long long len, int n, Ctl *ctl, cudaStream_t s) {
-    if (len <= 0) return cudaSuccess;
-    k_validate_batch<<<gsz(2 * len), BLK, 0, s>>>(batch, len, n, ctl);
+// The batch kernels read the batch and its length from the control block;
+// `len` only sizes their grid (a captured launch sequence is keyed by it).
+cudaError_t launch_validate_batch(long long len, int n, Ctl *ctl, cudaStream_t s) {
+    k_validate_batch<<<gsz(2 * len), BLK, 0, s>>>(n, ctl);
     return cudaGetLastError();
 }
-cudaError_t launch_ins_claim(const int *batch, long long len, Index ix, Ctl *ctl, u64 *nkey, u64 *nslot,
-                             cudaStream_t s) {
-    if (len <= 0) return cudaSuccess;
-    k_ins_claim<<<gsz(len), BLK, 0, s>>>(batch, len, ix, ctl, nkey, nslot);
+cudaError_t launch_ins_claim(long long len, Index ix, Ctl *ctl, u64 *nkey, u64 *nslot, cudaStream_t s) {
+    k_ins_claim<<<gsz(len), BLK, 0, s>>>(ix, ctl, nkey, nslot);
     return cudaGetLastError();
 }
 cudaError_t launch_ins_place(const Dev &d, const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, Index ix,
@@ -634,11 +638,9 @@ cudaError_t launch_ins_place(const Dev &d, const u64 *nkey, const u64 *nslot, Ct
         k_ins_place<false><<<d.grid, BLK, 0, s>>>(nkey, nslot, ctl, g, ix, ovf, ovf_cap, rep, pt, ck, ca, cb, cand_cap);
     return cudaGetLastError();
 }
-cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u64 *ovf, int *parent,
-                             const int *rep, Ctl *ctl, unsigned *aff_ep, unsigned *cut_ep, int *cutlist,
-                             unsigned *w, cudaStream_t s) {
-    if (len <= 0) return cudaSuccess;
-    k_del_claim<<<gsz(len), BLK, 0, s>>>(batch, len, ix, g, ovf, parent, rep, ctl, aff_ep, cut_ep, cutlist, w);
+cudaError_t launch_del_claim(long long len, Index ix, Csr g, u64 *ovf, int *parent, const int *rep, Ctl *ctl,
+                             unsigned *aff_ep, unsigned *cut_ep, int *cutlist, unsigned *w, cudaStream_t s) {
+    k_del_claim<<<gsz(len), BLK, 0, s>>>(ix, g, ovf, parent, rep, ctl, aff_ep, cut_ep, cutlist, w);
     return cudaGetLastError();
 }
 cudaError_t launch_scan_rows(const Dev &d, RowList rl, Ctl *ctl, Csr g, const int *rep, bool sg, PairTable pt,

@@ -29,13 +29,12 @@ cudaError_t launch_degree(const u64 *dkey, long long m, int *deg, cudaStream_t s
 cudaError_t launch_caps(const int *deg, int n, long long *cap, cudaStream_t s);
 cudaError_t launch_scan_i64(const long long *in, long long *out, long long n, long long *bsum, cudaStream_t s);
 cudaError_t launch_fill(const u64 *dkey, const u64 *dslot, long long m, Csr g, Index ix, cudaStream_t s);
-cudaError_t launch_validate_batch(const int *batch, long long len, int n, Ctl *ctl, cudaStream_t s);
-cudaError_t launch_ins_claim(const int *batch, long long len, Index ix, Ctl *ctl, u64 *nkey, u64 *nslot,
-                             cudaStream_t s);
+// (the batch kernels read the batch from the control block; len sizes the grid)
+cudaError_t launch_validate_batch(long long len, int n, Ctl *ctl, cudaStream_t s);
+cudaError_t launch_ins_claim(long long len, Index ix, Ctl *ctl, u64 *nkey, u64 *nslot, cudaStream_t s);
 
-cudaError_t launch_del_claim(const int *batch, long long len, Index ix, Csr g, u64 *ovf, int *parent,
-                             const int *rep, Ctl *ctl, unsigned *aff_ep, unsigned *cut_ep, int *cutlist,
-                             unsigned *w, cudaStream_t s);
+cudaError_t launch_del_claim(long long len, Index ix, Csr g, u64 *ovf, int *parent, const int *rep, Ctl *ctl,
+                             unsigned *aff_ep, unsigned *cut_ep, int *cutlist, unsigned *w, cudaStream_t s);
 // The rows a delete batch scans for cross edges, one entry per listed
 // vertex u: u itself, the exclusive prefix sum of the row lengths (roff[nd]
 // = total), the row's start in the CSR, and (rep[u], piece left out of the
@@ -70,7 +69,7 @@ cudaError_t launch_check_tree_edges(int n, const int *parent, Index ix, int *bad
 cudaError_t launch_check_cross(const int *pairs, long long m, const int *rep, int *bad, cudaStream_t s);
 
 // forest.cu ------------------------------------------------------------
-cudaError_t launch_begin(Ctl *ctl, int op, long long len, cudaStream_t s);
+cudaError_t launch_begin(Ctl *ctl, int op, long long len, const int *batch, cudaStream_t s);
 cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, int *A, int *rold,
                                unsigned *w, u64 *heavy, Ctl *ctl, const int *par, int *J, cudaStream_t s);
 cudaError_t launch_jump_async(const Dev &d, const int *A, Ctl *ctl, int *J, int *X, int *Y, cudaStream_t s);

@@ -233,3 +233,14 @@ def test_replacement_edge_variants(variant):
     run_trajectory(g, [(I, 1000), (D, 1000), (I, 10_000), (D, 10_000)] * 2, seed=3, flags=flags)
     g = workloads.grid_graph(512, 512, seed=3)
     run_trajectory(g, [(D, 5000), (I, 5000)] * 2, seed=4, tree_frac=0.9, local=64, flags=flags)
+
+
+def test_direct_launches_without_captured_graphs(monkeypatch):
+    """Batches are replayed from captured CUDA graphs by default; with
+    DRSF_GRAPHS=0 every kernel is launched one by one.  Both give the
+    oracle's forests (R-MAT-16 trajectory with a storage rebuild forced by
+    growth, which moves the storage the captured graphs point into)."""
+    g = workloads.rmat_graph(16, 16, seed=2)
+    for env in ("0", "1"):
+        monkeypatch.setenv("DRSF_GRAPHS", env)
+        run_trajectory(g, [(I, 1000), (D, 1000), (I, 60_000), (D, 10_000), (I, 200_000), (D, 50_000)], seed=3)
