@@ -51,8 +51,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="rmat22",
                    choices=["rmat22", "rmat20", "grid4096", "er-small", "batched256", "serving"])
-    p.add_argument("--requests", type=int, default=200, help="serving: requests in the trace")
+    p.add_argument("--requests", type=int, default=400, help="serving: requests in the trace")
     p.add_argument("--load", type=float, default=0.9, help="serving: arrival rate / synchronous capacity")
+    p.add_argument("--loads", default="0.5,0.7,0.9", help="serving: the load points of the latency curve")
     p.add_argument("--batch", type=int, default=0, help="batch size (default per workload)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -665,41 +666,68 @@ def run_serving(args, rank, ws, local):
     for h in hs0.values():
         h.close()
     cap = len(reqs) / (max(d.t_done for d in done0))
-    lam = args.load * cap
-    arr = np.cumsum(rng.exponential(1.0 / lam, len(reqs)))
-    timed = [serve.Request(r.rid, r.tenant, r.op, r.batch, float(a)) for r, a in zip(reqs, arr)]
-    done_s, hs1 = serve.run_synchronous(tenants, timed)
-    sync_final = {t: h.parent().cpu().numpy() for t, h in hs1.items()}
-    for h in hs1.values():
+
+    def new_server():
+        srv = serve.Server(budget_bytes=120 << 30, slots=8, coalesce=True, reserve_edges=1_000_000)
+        for t, (n, e, p) in tenants.items():
+            srv.add_tenant(t, n, e, p)
+        srv.admit_all()
+        return srv
+
+    def close_server(srv):
+        srv.close()
+
+    # warm-up of both forms (first launches, captures, allocator) on the
+    # first quarter of the trace, not timed
+    warm = reqs[: max(1, len(reqs) // 4)]
+    _, hw = serve.run_synchronous(tenants, warm)
+    for h in hw.values():
         h.close()
-    srv = serve.Server(budget_bytes=120 << 30, slots=8, coalesce=True)
-    for t, (n, e, p) in tenants.items():
-        srv.add_tenant(t, n, e, p)
-    srv.admit_all()
-    done_c = srv.run(timed)
-    # each tenant's result in the mix equals its applied log replayed alone
-    same = True
-    for t, g in graphs.items():
-        _, par_mix = srv.state(t)
-        f = drsf.DynamicForest(g.n, torch.from_numpy(g.edges()).cuda(), torch.from_numpy(g.parent).cuda())
-        for op, b in srv.tenants[t].log:
-            f.apply_host(op, b)
-        same &= bool(np.array_equal(f.parent().cpu().numpy(), par_mix))
-        f.close()
+    srv_w = new_server()
+    srv_w.run(warm)
+    close_server(srv_w)
+    # the latency curve: Poisson arrivals at each load (x synchronous
+    # capacity), server and synchronous apply on the same trace
+    loads = [float(x) for x in args.loads.split(",") if x] or [args.load]
+    if args.load not in loads:
+        loads.append(args.load)
+    curve = {}
+    same = None
+    srv_main = sy_main = None
+    for load in loads:
+        lam = load * cap
+        arr = np.cumsum(np.random.default_rng(5 + int(load * 100)).exponential(1.0 / lam, len(reqs)))
+        timed = [serve.Request(r.rid, r.tenant, r.op, r.batch, float(a)) for r, a in zip(reqs, arr)]
+        done_s, hs1 = serve.run_synchronous(tenants, timed)
+        for h in hs1.values():
+            h.close()
+        srv = new_server()
+        done_c = srv.run(timed)
+        sv, sy = serve.summarize(done_c), serve.summarize(done_s)
+        curve[str(load)] = {"arrival_rate_per_s": round(lam, 2), "server": sv, "synchronous": sy}
+        if load == args.load:
+            srv_main, sy_main = sv, sy
+            # each tenant's result in the mix equals its applied log replayed alone
+            same = True
+            for t, g in graphs.items():
+                _, par_mix = srv.state(t)
+                f = drsf.DynamicForest(g.n, torch.from_numpy(g.edges()).cuda(), torch.from_numpy(g.parent).cuda())
+                for op, b in srv.tenants[t].log:
+                    f.apply_host(op, b)
+                same &= bool(np.array_equal(f.parent().cpu().numpy(), par_mix))
+                f.close()
+            coalesced = int(sum(len(t.log) for t in srv.tenants.values()))
+            evictions = srv.evictions
+        close_server(srv)
     # saturation: everything queued at time 0 (capacity of each form)
-    srv2 = serve.Server(budget_bytes=120 << 30, slots=8, coalesce=True)
-    for t, (n, e, p) in tenants.items():
-        srv2.add_tenant(t, n, e, p)
-    srv2.admit_all()
+    srv2 = new_server()
     done_c0 = srv2.run(reqs)
-    for t in srv2.tenants.values():
-        if t.handle is not None:
-            t.handle.close()
+    close_server(srv2)
     cap_server = serve.summarize(done_c0)
     cap_sync = serve.summarize(done0)
-    sv, sy = serve.summarize(done_c), serve.summarize(done_s)
     if rank != 0:
         return
+    sv, sy = srv_main, sy_main
     line = {"metric": "serving: sustained updates/s and batch latency (resident R-MAT-22 + 64 tenants)",
             "value": sv["updates_per_s"], "unit": UNIT, "n_gpus": ws, "steps": len(reqs), "warmup": 0,
             "ms_per_step": round(sv["makespan_s"] / len(reqs) * 1e3, 4), "higher_is_better": True,
@@ -707,16 +735,16 @@ def run_serving(args, rank, ws, local):
             "config": {"workload": "resident R-MAT scale 22 + 64 R-MAT tenants (scales 14-18), 120 GB budget; "
                                    "Poisson arrivals, sizes log-uniform [100, 1M], 60/40 insert/delete, "
                                    "tenant Zipf(1.1), seed 5", "requests": len(reqs),
-                       "arrival_rate_per_s": round(lam, 2), "load_vs_sync_capacity": args.load,
-                       "slots": 8, "coalescing": True},
-            "server": sv, "synchronous": sy,
+                       "load_vs_sync_capacity": args.load, "slots": 8, "coalescing": True,
+                       "big_batch_priority_stream": ">= 50,000 edges", "reserved_batch_edges": 1_000_000,
+                       "streams": "one own stream per tenant (+ one high-priority stream for big batches)"},
+            "server": sv, "synchronous": sy, "latency_curve": curve,
             "capacity": {"server_updates_per_s": cap_server["updates_per_s"],
                          "synchronous_updates_per_s": cap_sync["updates_per_s"],
                          "server_over_sync": round(cap_server["updates_per_s"] / cap_sync["updates_per_s"], 3),
                          "what": "all requests queued at time 0"},
             "server_over_sync_updates_per_s": round(sv["updates_per_s"] / sy["updates_per_s"], 3),
-            "coalesced_batches": int(sum(len(t.log) for t in srv.tenants.values())),
-            "evictions": srv.evictions, "results_identical_to_alone": same}
+            "coalesced_batches": coalesced, "evictions": evictions, "results_identical_to_alone": same}
     print(json.dumps(line), flush=True)
 
 

@@ -248,6 +248,29 @@ DRSF_API drsf_status drsf_apply_batched(drsf_handle h, drsf_op op, const int32_t
                                         const int64_t *batch_offsets, const drsf_batched_class *classes,
                                         int32_t num_classes, drsf_stream stream);
 
+/*
+ * drsf_reserve -- size the handle's per-batch buffers (device work lists,
+ * pair table, the pinned host staging of drsf_apply_host) for batches of up
+ * to max_batch edges now, so that later drsf_apply / drsf_apply_host calls
+ * of at most that size neither allocate nor synchronise for them (storage
+ * growth of the graph itself can still do so).  Not in the paper: for
+ * serving loops, where an allocation or a synchronisation inside one
+ * tenant's call stalls every other tenant's work.  Synchronises `stream`.
+ * Errors: DRSF_EINVAL, DRSF_ENOMEM, DRSF_ECUDA, DRSF_EPOISONED.
+ */
+DRSF_API drsf_status drsf_reserve(drsf_handle h, int64_t max_batch, drsf_stream stream);
+
+/*
+ * drsf_stream_create / drsf_stream_destroy -- a CUDA stream of the caller's
+ * own (non-blocking, priority clamped to the device's range; a smaller
+ * number is a higher priority).  Not in the paper: a serving loop gives
+ * every tenant its own streams, where a framework's stream pool would let
+ * two tenants share one and queue behind each other.  The caller destroys
+ * what it created.  Errors: DRSF_EINVAL, DRSF_ECUDA.
+ */
+DRSF_API drsf_status drsf_stream_create(int priority, drsf_stream *out);
+DRSF_API drsf_status drsf_stream_destroy(drsf_stream stream);
+
 /* drsf_parent -- the output of the D-RSF problem (problem box, Section I):
  * the rooted spanning forest F' of the updated graph G', as parent
  * pointers.  Copies

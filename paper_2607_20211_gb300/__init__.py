@@ -149,6 +149,12 @@ def _load():
         lib.drsf_selftest_barrier_timeout.argtypes = [vp]
         lib.drsf_phase_name.restype = ctypes.c_char_p
         lib.drsf_phase_name.argtypes = [ctypes.c_int]
+        lib.drsf_stream_create.restype = ctypes.c_int
+        lib.drsf_stream_create.argtypes = [ctypes.c_int, P(vp)]
+        lib.drsf_stream_destroy.restype = ctypes.c_int
+        lib.drsf_stream_destroy.argtypes = [vp]
+        lib.drsf_reserve.restype = ctypes.c_int
+        lib.drsf_reserve.argtypes = [vp, i64, vp]
         lib.drsf_apply_batched.restype = ctypes.c_int
         lib.drsf_apply_batched.argtypes = [vp, ctypes.c_int, vp, i64, i32, vp, vp, vp, i32, vp]
         _lib = lib
@@ -175,6 +181,27 @@ def use_torch_allocator(enable: bool = True) -> None:
 def selftest_barrier_timeout(stream=None) -> int:
     """Run the bounded-wait self-test; returns the status (ETIMEOUT expected)."""
     return int(_load().drsf_selftest_barrier_timeout(_stream_ptr(stream)))
+
+
+class OwnStream:
+    """A CUDA stream of its own (not from torch's stream pool, which hands
+    the same few streams to every caller), usable as a torch stream through
+    `.torch`; destroyed by close().  priority: a smaller number is a higher
+    priority (clamped to the device's range)."""
+
+    def __init__(self, priority: int = 0):
+        p = ctypes.c_void_p()
+        st = _load().drsf_stream_create(int(priority), ctypes.byref(p))
+        if st:
+            raise DRSFError(st, "drsf_stream_create")
+        self.ptr = p.value
+        self.torch = torch.cuda.ExternalStream(self.ptr)
+
+    def close(self) -> None:
+        if self.ptr:
+            torch.cuda.synchronize()
+            _load().drsf_stream_destroy(self.ptr)
+            self.ptr = None
 
 
 def _stream_ptr(stream) -> int:
@@ -259,6 +286,13 @@ class DynamicForest:
                                      len(classes), _stream_ptr(self._stream))
         if st:
             raise DRSFError(st, "drsf_apply_batched")
+
+    def reserve(self, max_batch: int) -> None:
+        """Size the per-batch buffers for batches of up to max_batch edges
+        now (no allocation or synchronisation for them later)."""
+        st = _lib.drsf_reserve(self._h, int(max_batch), _stream_ptr(self._stream))
+        if st:
+            raise DRSFError(st, "drsf_reserve")
 
     def insert(self, batch: torch.Tensor) -> None:
         self.apply(INSERT, batch)

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -39,6 +40,7 @@ struct drsf_ctx {
     // captured per-batch launch sequences (CUDA graphs), valid for storage
     // generation u_gen; gen moves whenever a storage or batch buffer moves
     std::vector<std::pair<std::string, cudaGraphExec_t>> u_graphs;
+    std::map<std::string, int> u_seen;   // uses of each shape (capture on the second)
     long long gen = 0, u_gen = 0;
     bool graphs_ok = true;
     cudaStream_t u_cap = nullptr;
@@ -808,6 +810,7 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
     while (glen < len) glen <<= 2;
     if (h->u_gen != h->gen) {
         drop_graphs(h);
+        h->u_seen.clear();
         h->u_gen = h->gen;
     }
     const std::string key = std::to_string(op) + ":" + std::to_string(sg ? 1 : 0) + ":" + std::to_string(glen);
@@ -815,6 +818,12 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
     for (auto &ge : h->u_graphs)
         if (ge.first == key) exec = ge.second;
     if (!exec) {
+        // a shape is captured on its second use: recording and instantiating
+        // costs more host time than one direct launch sequence, and a
+        // handle that sees a shape once (a tenant with few batches) never
+        // pays it
+        int &seen = h->u_seen[key];
+        if (++seen < 2) return launch_rest(h, op, sg, len, s);
         // recorded on a stream of the library's own (the caller's stream may
         // be the legacy default stream, which cannot be captured); nothing
         // runs while recording, the replay below is ordered on s
@@ -1080,12 +1089,8 @@ drsf_status drsf_apply(drsf_handle h, drsf_op op, const int32_t *batch, int64_t 
     return apply_impl(h, (int)op, batch, len, (cudaStream_t)stream);
 }
 
-drsf_status drsf_apply_host(drsf_handle h, drsf_op op, const int32_t *batch, int64_t len, drsf_stream stream) {
-    if (!h || (op != DRSF_INSERT && op != DRSF_DELETE) || len < 0 || (len > 0 && !batch)) return DRSF_EINVAL;
-    if (h->poisoned) return DRSF_EPOISONED;
-    if (len > (int64_t)1 << 31) return DRSF_EINVAL;
-    set_dev(h);
-    cudaStream_t s = (cudaStream_t)stream;
+// Host staging of drsf_apply_host sized for `len` edges (grows only).
+static drsf_status ensure_stage(drsf_ctx *h, long long len, cudaStream_t s) {
     if (len > h->stage_cap) {
         CK(cudaStreamSynchronize(s));
         if (h->stage_host) cudaFreeHost(h->stage_host);
@@ -1098,6 +1103,30 @@ drsf_status drsf_apply_host(drsf_handle h, drsf_op op, const int32_t *batch, int
         if (!h->stage_done) CK(cudaEventCreateWithFlags(&h->stage_done, cudaEventDisableTiming));
         h->stage_pending = false;
     }
+    return DRSF_OK;
+}
+
+drsf_status drsf_reserve(drsf_handle h, int64_t max_batch, drsf_stream stream) {
+    if (!h || max_batch < 0 || max_batch > (int64_t)1 << 31) return DRSF_EINVAL;
+    if (h->poisoned) return DRSF_EPOISONED;
+    set_dev(h);
+    cudaStream_t s = (cudaStream_t)stream;
+    drsf_status st = ensure_batch(h, max_batch, s);
+    if (st) return st;
+    st = ensure_stage(h, max_batch, s);
+    if (st) return st;
+    CK(cudaStreamSynchronize(s));
+    return DRSF_OK;
+}
+
+drsf_status drsf_apply_host(drsf_handle h, drsf_op op, const int32_t *batch, int64_t len, drsf_stream stream) {
+    if (!h || (op != DRSF_INSERT && op != DRSF_DELETE) || len < 0 || (len > 0 && !batch)) return DRSF_EINVAL;
+    if (h->poisoned) return DRSF_EPOISONED;
+    if (len > (int64_t)1 << 31) return DRSF_EINVAL;
+    set_dev(h);
+    cudaStream_t s = (cudaStream_t)stream;
+    drsf_status st = ensure_stage(h, len, s);
+    if (st) return st;
     if (h->stage_pending) CK(cudaEventSynchronize(h->stage_done));   // previous copy out of the staging buffer
     if (len > 0) {
         memcpy(h->stage_host, batch, (size_t)len * 2 * sizeof(int));
@@ -1264,6 +1293,26 @@ drsf_status drsf_static_forest(drsf_handle h, int32_t *parent_out, int32_t *labe
         CK(cudaStreamSynchronize(s));
         *levels_out = lv;
     }
+    return DRSF_OK;
+}
+
+drsf_status drsf_stream_create(int priority, drsf_stream *out) {
+    if (!out) return DRSF_EINVAL;
+    *out = nullptr;
+    int lo = 0, hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    // the runtime's range runs from lo (lowest) to hi (highest, numerically
+    // smaller); clamp the request into it
+    int p = priority < hi ? hi : (priority > lo ? lo : priority);
+    cudaStream_t s = nullptr;
+    CK(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, p));
+    *out = (drsf_stream)s;
+    return DRSF_OK;
+}
+
+drsf_status drsf_stream_destroy(drsf_stream stream) {
+    if (!stream) return DRSF_EINVAL;
+    CK(cudaStreamDestroy((cudaStream_t)stream));
     return DRSF_OK;
 }
 

@@ -81,3 +81,37 @@ def test_mix_equals_alone(coalesce, budget):
         assert s.evictions > 0
     stats = serve.summarize(done)
     assert stats["requests"] == len(reqs)
+
+
+def test_coalesced_mix_keeps_labels_and_validity_per_request_sequence():
+    """With coalescing, a tenant's forest in the mix is its coalesced log
+    replayed alone (tested above); against its original request sequence
+    applied one by one, the labels must be identical and the mix's forest
+    must be a valid rooted spanning forest of the same graph (a merged batch
+    may pick other replacement edges, so the parent arrays may differ)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    drsf.build()
+    graphs = _tenants(4, seed=80)
+    reqs = _trace(graphs, per_tenant=10, seed=81, spread=0.001)
+    s = serve.Server(budget_bytes=120 << 30, slots=4, coalesce=True)
+    for tid, g in graphs.items():
+        s.add_tenant(tid, g.n, g.edges(), g.parent)
+    s.run(reqs)
+    for tid, g in graphs.items():
+        keys, par = g.keys, g.parent
+        for r in sorted((r for r in reqs if r.tenant == tid), key=lambda r: (r.t_arrive, r.rid)):
+            o = oracle.apply(g.n, keys, par, r.op, r.batch, want_keys=True)
+            keys, par = o.keys, o.parent
+        _, par_mix = s.state(tid)
+        assert oracle.check_forest(g.n, keys, par_mix) == 0, tid
+        lab_mix = oracle.labels(g.n, keys)
+        # labels from the mix's own forest: the smallest vertex id of each tree
+        v = np.arange(g.n)
+        roots = par_mix.copy()
+        for _ in range(40):   # pointer doubling: depth up to 2^40
+            roots = roots[roots]
+        mins = np.full(g.n, g.n, np.int64)
+        np.minimum.at(mins, roots, v)
+        assert np.array_equal(mins[roots], lab_mix), tid
+    s.close()
