@@ -216,6 +216,12 @@ def phase_bytes(st: dict, n: int, op: int) -> dict:
         # each doubling step taken (a visit: read J, gather J[J], write) counts
         # 12 bytes; the steps taken stay below affected x doubling rounds
         out["jump"] = 12 * st.get("jump_visits", aff * max(st["jump_rounds"], 1))
+        if st.get("detach_levels", 0) > 0:
+            # top-down search instead of pointer jumping: per scanned entry
+            # the column and the parent gather, per detached vertex its
+            # representative, list slot and row record
+            out["jump"] = 8 * st["detach_entries"] + 24 * aff
+            out["affected"] = 0
         out["scan"] = 12 * st["detached"] + 8 * st["scanned"] + 8 * st["candidates"]
         out["active"] = 8 * aff
     c, ner = st["candidates"], st["replacement"]
@@ -395,7 +401,8 @@ def run_ours(args, rank, ws, local):
         return round(float(np.mean([steps[W + k][op][1][key] for k in range(K)])), 1)
     batch_stats = {oname: {key: _mean(op, key) for key in (
         "applied", "tree_cut", "affected", "detached", "scanned", "candidates", "hook_rounds", "replacement",
-        "rank_rounds", "active", "reversed", "mark_rounds", "jump_rounds", "jump_visits")} for op, oname in ((0, "insert"),
+        "rank_rounds", "active", "reversed", "mark_rounds", "jump_rounds", "jump_visits", "detach_levels",
+        "detach_entries")} for op, oname in ((0, "insert"),
                                                                                         (1, "delete"))}
 
     # end to end through the C ABI with host buffers

@@ -150,6 +150,10 @@ typedef struct {
     int64_t jump_visits;   /* vertex visits summed over the pointer-jumping steps */
     int64_t supergraph;    /* 1: the batch took the supergraph (SG) variant,
                               0: hooking on every cross edge (HS) */
+    int64_t detach_levels; /* delete: levels of the top-down search for the
+                              detached vertices (0: none, negative: it ran
+                              over its budget and pointer jumping took over) */
+    int64_t detach_entries;/* delete: adjacency entries that search read */
 } drsf_batch_stats;
 
 /* Allocator hooks.  alloc(bytes, stream, ctx) returns device memory or NULL;
@@ -177,7 +181,13 @@ DRSF_API drsf_status drsf_set_allocator(drsf_alloc_fn alloc, drsf_free_fn free_f
  * the handle's delete batches: unset, asynchronous pointer doubling (per-warp
  * slices stepping in place, no grid barrier between steps); "sync",
  * synchronous doubling rounds; "halving", path-halving walks.  All three give
- * the same representatives.
+ * the same representatives.  Before it, a delete batch first looks for its
+ * detached vertices top-down from the cut vertices over tree children
+ * (touching only the detached vertices' rows) and falls back to the root
+ * search only when that search exceeds its budget; DRSF_DETACH=0 skips the
+ * top-down search, DRSF_DETACH_MAX (default 32768) is the longest delete
+ * batch that tries it.  DRSF_GRAPHS=0 launches every batch's kernels directly
+ * instead of replaying a captured CUDA graph.
  * Errors: DRSF_EINVAL (n out of range, negative m, NULL pointers, an id out
  * of range), DRSF_ENOMEM, DRSF_ECUDA, DRSF_ENOT_FOREST.
  */

@@ -47,7 +47,8 @@ class BatchStats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in (
         "batch_len", "self_loops", "dropped", "applied", "tree_cut", "affected", "detached", "scanned",
         "candidates", "hook_rounds", "replacement", "rank_rounds", "active", "reversed", "mark_rounds",
-        "jump_rounds", "edges", "overflow", "rebuilds", "jump_visits", "supergraph")]
+        "jump_rounds", "edges", "overflow", "rebuilds", "jump_visits", "supergraph", "detach_levels",
+        "detach_entries")]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -64,6 +64,10 @@ struct drsf_ctx {
     int *chx = nullptr, *chy = nullptr;
     unsigned *aff_ep = nullptr, *cut_ep = nullptr, *pstamp = nullptr, *att_ep = nullptr, *rep_ep = nullptr;
     unsigned *long_ep = nullptr, *hstamp = nullptr;
+    unsigned *det_ep = nullptr, *det_claim = nullptr;   // top-down delete stamps
+    bool detach = true;                                 // DRSF_DETACH=0 turns the top-down delete off
+    long long detach_max = 1 << 15;                     // ... and it runs for batches up to this length
+    bool detach_now = false;                            // this batch's choice
     u64 *best0 = nullptr, *best1 = nullptr, *er = nullptr, *heavy = nullptr;
     int *rold = nullptr, *cdeg = nullptr, *xlist = nullptr, *aidx = nullptr, *aroot = nullptr;
     int *oep = nullptr, *oeid = nullptr, *oeroot = nullptr;
@@ -462,6 +466,8 @@ static drsf_status alloc_work(drsf_ctx *h, cudaStream_t s) {
     CKA(halloc(h, &h->long_ep, n, s));
     CKA(halloc(h, &h->hstamp, n, s));
     CKA(halloc(h, &h->rep_ep, n, s));
+    CKA(halloc(h, &h->det_ep, n, s));
+    CKA(halloc(h, &h->det_claim, n, s));
     CKA(halloc(h, &h->best0, n, s));
     CKA(halloc(h, &h->best1, n, s));
     CKA(halloc(h, &h->heavy, n, s));
@@ -491,7 +497,8 @@ static drsf_status alloc_work(drsf_ctx *h, cudaStream_t s) {
     CKA(halloc(h, &h->nx1, 2 * n + 2, s));
     CKA(halloc(h, &h->bsum, 8192, s));
     CKA(halloc(h, &h->ctl, 1, s));
-    unsigned *eps[] = {h->aff_ep, h->cut_ep, h->pstamp, h->att_ep, h->rep_ep, h->long_ep, h->hstamp};
+    unsigned *eps[] = {h->aff_ep, h->cut_ep, h->pstamp, h->att_ep, h->rep_ep, h->long_ep, h->hstamp, h->det_ep,
+                       h->det_claim};
     for (unsigned *e : eps) CK(cudaMemsetAsync(e, 0, n * sizeof(unsigned), s));
     CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
     return DRSF_OK;
@@ -622,6 +629,7 @@ drsf_status drsf_create(int32_t n, const int32_t *edges, int64_t m, const int32_
     h->dev.grid_scan = scan_grid(nsm);
     h->dev.grid_pass = grid_vertex_pass(nsm);
     h->dev.coop_et = coop_blocks_et(nsm);
+    h->dev.coop_detach = coop_blocks_detach(nsm);
     // root search of a delete batch: barrier-free doubling over per-warp
     // slices by default; DRSF_JUMP=sync selects synchronous doubling rounds,
     // DRSF_JUMP=halving the in-place path-halving walks
@@ -631,6 +639,13 @@ drsf_status drsf_create(int32_t n, const int32_t *edges, int64_t m, const int32_
     // replaying a captured CUDA graph
     const char *gr = getenv("DRSF_GRAPHS");
     h->graphs_ok = !(gr && strcmp(gr, "0") == 0);
+    // DRSF_DETACH=0: deletes find their detached vertices by pointer jumping
+    // over the cut trees only (no top-down search first)
+    const char *dt = getenv("DRSF_DETACH");
+    h->detach = !(dt && strcmp(dt, "0") == 0);
+    // DRSF_DETACH_MAX: the largest delete batch that tries it first
+    const char *dm = getenv("DRSF_DETACH_MAX");
+    if (dm) h->detach_max = atoll(dm);
     drsf_status st = create_impl(h, edges, m, parent, s);
     if (st != DRSF_OK) {
         destroy_all(h);
@@ -679,11 +694,21 @@ static drsf_status launch_rest(drsf_ctx *h, int op, bool sg, long long glen, cud
         // Algorithm 1, delete: remove B, cut tree edges, re-label the cut trees
         prof_begin(h, PH_DEL_CLAIM, s);
         CK(launch_del_claim(glen, h->ix, g, h->ovf, h->parent, h->rep, ctl, h->aff_ep, h->cut_ep, h->cutlist,
-                            h->wgt, s));
+                            h->wgt, h->rold, s));
         prof_end(h, PH_DEL_CLAIM, 1, s);
+        if (h->detach_now) {
+            // the detached vertices top-down from the cut vertices; over its
+            // budget it hands over to the pointer jumping below
+            prof_begin(h, PH_JUMP, s);
+            const long long n = h->n;
+            CK(launch_detach(h->dev, ctl, h->cutlist, h->parent, h->rep, g, h->ovf, h->ovf_cap, rows(h), h->A, h->J1,
+                             h->det_ep, h->det_claim, h->rold, std::max<long long>(1 << 16, n / 8),
+                             std::max<long long>(1 << 20, 4 * n), 256, h->act, h->xlist, s));
+            prof_end(h, PH_JUMP, 1, s);
+        }
         prof_begin(h, PH_AFF, s);
         CK(launch_aff_collect(h->dev, h->n, h->rep, h->aff_ep, h->A, h->rold, h->wgt, h->heavy, ctl, h->parent,
-                              h->jump_sync == 2 ? h->J0 : nullptr, s));
+                              h->jump_sync == 2 ? h->J0 : nullptr, 0, s));
         prof_end(h, PH_AFF, 1, s);
         prof_begin(h, PH_JUMP, s);
         if (h->jump_sync == 2) CK(launch_jump_async(h->dev, h->A, ctl, h->J0, h->act, h->xlist, s));
@@ -744,6 +769,13 @@ static drsf_status launch_rest(drsf_ctx *h, int op, bool sg, long long glen, cud
     }
     const unsigned *sel = euler ? h->att_ep : h->long_ep;
     prof_begin(h, PH_ACTIVE, s);
+    if (op == DRSF_DELETE && h->detach_now) {
+        // after a top-down delete the affected list holds the detached
+        // vertices only; a root piece that was re-rooted adds its vertices
+        CK(launch_rootcheck(h->dev, ctl, h->cutlist, h->rold, h->rep_ep, s));
+        CK(launch_aff_collect(h->dev, h->n, h->rep, h->aff_ep, h->A, h->rold, h->wgt, h->heavy, ctl, h->parent,
+                              nullptr, 1, s));
+    }
     if (op == DRSF_INSERT)
         CK(launch_active(h->dev, nullptr, 0, h->n, ctl, h->rep, h->parent, sel, h->att_x, h->rep_ep, h->newrep,
                          h->act, h->pold, h->J0, h->mark, h->aidx, h->aroot, s));
@@ -795,6 +827,9 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
     if (st) return st;
     const bool sg = use_supergraph(h, op, len);
     h->last_sg = sg ? 1 : 0;
+    // the top-down delete for small batches: its cost follows the detached
+    // vertices' rows and its levels, the pointer jumping's the cut trees
+    h->detach_now = op == DRSF_DELETE && h->detach && len <= h->detach_max;
     if (h->prof_on) {
         h->prof_batches++;
         h->prof_op = op;
@@ -813,7 +848,8 @@ static drsf_status apply_impl(drsf_ctx *h, int op, const int32_t *batch, int64_t
         h->u_seen.clear();
         h->u_gen = h->gen;
     }
-    const std::string key = std::to_string(op) + ":" + std::to_string(sg ? 1 : 0) + ":" + std::to_string(glen);
+    const std::string key = std::to_string(op) + ":" + std::to_string(sg ? 1 : 0) + ":" + std::to_string(glen) +
+                            ":" + std::to_string(h->detach_now ? 1 : 0);
     cudaGraphExec_t exec = nullptr;
     for (auto &ge : h->u_graphs)
         if (ge.first == key) exec = ge.second;
@@ -1206,6 +1242,8 @@ drsf_status drsf_stats(drsf_handle h, drsf_batch_stats *out, drsf_stream stream)
     out->rebuilds = h->rebuilds;
     out->jump_visits = c.jump_visits;
     out->supergraph = h->last_sg;
+    out->detach_levels = c.det_levels;
+    out->detach_entries = c.det_entries;
     return latched(h);
 }
 

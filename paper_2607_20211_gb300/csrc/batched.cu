@@ -861,8 +861,10 @@ __global__ void k_bbegin(const BState *Sp) {
         ctl->scanned = ctl->self_loops = ctl->dropped = ctl->tree_cut = 0;
         ctl->hook_rounds = ctl->rank_rounds = ctl->mark_rounds = ctl->jump_rounds = ctl->reversed = 0;
         ctl->jump_visits = 0;
+        ctl->td = ctl->need_root = 0;
+        ctl->det_levels = ctl->det_entries = 0;
         ctl->batch_len = d.len;
-        for (int i = 0; i < 6; ++i) ctl->bar[i] = 0;
+        for (int i = 0; i < 8; ++i) ctl->bar[i] = 0;
         *S.pool_ctr = 0;
     }
     if (threadIdx.x < BCLASSES) S.qctr[threadIdx.x] = 0;

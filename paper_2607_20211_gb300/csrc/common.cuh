@@ -45,10 +45,13 @@ struct Ctl {
     int skip;               // current batch rejected (ERR_BATCH_ID seen)
     unsigned epoch;         // batch counter; epoch stamps compare against it
     int op;
-    u64 bar[6];             // grid-barrier counters: jump, hook, orient, mark, bfs, Euler marks
+    u64 bar[8];             // grid-barrier counters: jump, hook, orient, mark, bfs, Euler marks, detach
                             // (reset at each batch's start and before each static BFS)
     int flag[3];            // per-round "another round needed" flags
     u64 cnt[3];             // per-round list sizes (hook-and-compress)
+    u64 dv[3], dp[3];       // top-down delete, per level (ring of 3): vertices appended, and
+                            // rows << 32 | entries appended
+    u64 dovf;               // top-down delete: tree edges listed from the overflow list
     u64 nb;                 // normalised batch edges (new / deleted keys)
     u64 ncut;               // cut vertices
     u64 naff;               // affected list
@@ -75,6 +78,10 @@ struct Ctl {
     long long batch_len;
     long long overflow_total;
     const int *batch;       // the current batch (device), set by k_begin
+    int td;                 // delete: the detached vertices were found top-down (else: pointer jumping)
+    int need_root;          // delete, top-down: a tree's root piece is re-rooted (list its vertices)
+    long long det_levels;   // top-down levels of the batch (0: not taken)
+    long long det_entries;  // adjacency entries the top-down search read
 };
 
 // The edge index.

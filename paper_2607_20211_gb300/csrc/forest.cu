@@ -73,16 +73,20 @@ __global__ void k_begin(Ctl *ctl, int op, long long len, const int *batch) {
     ctl->scanned = ctl->self_loops = ctl->dropped = ctl->tree_cut = 0;
     ctl->hook_rounds = ctl->rank_rounds = ctl->mark_rounds = ctl->jump_rounds = ctl->reversed = 0;
     ctl->jump_visits = 0;
+    ctl->td = ctl->need_root = 0;
+    ctl->det_levels = ctl->det_entries = 0;
     ctl->batch_len = len;
     for (int i = 0; i < 3; ++i) {
         ctl->flag[i] = 0;
         ctl->cnt[i] = 0;
+        ctl->dv[i] = ctl->dp[i] = 0;
     }
+    ctl->dovf = 0;
     // each barrier counter serves one cooperative launch per batch; its
     // targets are multiples of that launch's grid size, so it restarts at 0
     // (launches of different grid sizes, or a wait that timed out, leave it
     // at any value)
-    for (int i = 0; i < 6; ++i) ctl->bar[i] = 0;
+    for (int i = 0; i < 8; ++i) ctl->bar[i] = 0;
 }
 
 // Delete: list the vertices of every tree that lost a tree edge (its old
@@ -90,9 +94,16 @@ __global__ void k_begin(Ctl *ctl, int op, long long len, const int *batch) {
 // Each thread takes IPT consecutive vertices per iteration (one vector load
 // of rep, IPT gathers in flight) and the block reserves its list slots with
 // one atomic; the list stays in vertex order.
+// With roots_only (after a top-down search of the detached vertices, when
+// some tree's root piece is re-rooted) only the root pieces' vertices are
+// appended (the detached ones already hold their new representative, which
+// is no stamped old root); otherwise the pass runs only when the top-down
+// search did not (the pointer-jumping path).
 __global__ void k_aff_collect(int n, const int *rep, const unsigned *aff_ep, int *A, int *rold, unsigned *w,
-                              u64 *heavy, Ctl *ctl, const int *par, int *J) {
+                              u64 *heavy, Ctl *ctl, const int *par, int *J, int roots_only) {
     if (*(volatile int *)&ctl->skip) return;
+    if (roots_only ? !(*(volatile int *)&ctl->td && *(volatile int *)&ctl->need_root) : *(volatile int *)&ctl->td)
+        return;
     unsigned ep = ctl->epoch;
     const long long step = (long long)gridDim.x * blockDim.x * IPT;
     for (long long b0 = (long long)blockIdx.x * blockDim.x * IPT; b0 < n; b0 += step) {
@@ -112,6 +123,7 @@ __global__ void k_aff_collect(int n, const int *rep, const unsigned *aff_ep, int
             if (!in[k]) continue;
             const int v = (int)(v0 + k);
             A[p++] = v;
+            if (roots_only) continue;
             rold[v] = r[k];
             if (J) J[v] = par[v];   // seed of the asynchronous doubling
             if (r[k] == v) {   // the old root: piece-weight and heaviest-piece slots
@@ -166,7 +178,7 @@ __device__ __noinline__ void fill_tiles(int *tile, long long st, long long d, in
 // the cut forest for the listed vertices; afterwards J[v] is the complemented
 // root of every listed vertex, and k_jump<2> carries on from there.
 __global__ void __launch_bounds__(BLK, 6) k_jump_async(const int *A, Ctl *ctl, int *J, int *X, int *Y) {
-    if (*(volatile int *)&ctl->skip) return;
+    if (*(volatile int *)&ctl->skip || *(volatile int *)&ctl->td) return;
     const long long cnt = (long long)ctl->naff;
     // asynchronous doubling in place (one buffer, no grid barrier
     // between steps): each warp owns a slice of the list and repeats
@@ -236,6 +248,252 @@ __global__ void __launch_bounds__(BLK, 6) k_jump_async(const int *A, Ctl *ctl, i
     }
 }
 
+// Warp-aggregated list appends of the top-down search (no block barrier):
+// the calling lanes with `on` take consecutive slots of A, those with a
+// non-empty row (`len` > 0) consecutive rows of the row list and their entry
+// ranges, from one atomic per warp on each counter (rows in the high and
+// entries in the low 32 bits of the packed row counter).  All 32 lanes call.
+// Append one warp's detached vertices (lanes with `on`) to the vertex list
+// and their non-empty rows to the row list of the scan: positions are the
+// level's bases (vb vertices; pb rows << 32 | entries) plus offsets taken
+// from the level's own counters (vc, pc), one atomic per warp on each.
+__device__ __forceinline__ void warp_detach_append(u64 *vc, u64 *pc, long long vb, u64 pb, RowList rl, int *A, Csr g,
+                                                   bool on, int w, int len, int p, int ro) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned m = __ballot_sync(0xffffffffu, on);
+    if (!m) return;
+    const int ld = __ffs(m) - 1;
+    u64 a0 = 0;
+    if (lane == ld) a0 = atomicAdd(vc, (u64)__popc(m));
+    a0 = __shfl_sync(0xffffffffu, a0, ld);
+    if (on) A[vb + (long long)a0 + __popc(m & lt)] = w;
+    const bool f = on && len > 0;
+    const unsigned fm = __ballot_sync(0xffffffffu, f);
+    if (!fm) return;
+    // exclusive warp scan of the row lengths
+    int x = f ? len : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const int tot = __shfl_sync(0xffffffffu, x, 31);
+    const int ex = x - (f ? len : 0);
+    const int fl = __ffs(fm) - 1;
+    u64 base = 0;
+    if (lane == fl) base = atomicAdd(pc, ((u64)__popc(fm) << 32) | (u64)(unsigned)tot);
+    base = __shfl_sync(0xffffffffu, base, fl) + pb;
+    if (f) {
+        const long long q = (long long)(base >> 32) + __popc(fm & lt);
+        const long long eo = (long long)(base & 0xFFFFFFFFull) + ex;
+        rl.D[q] = w;
+        rl.roff[q] = (unsigned)eo;
+        rl.base[q] = (unsigned)g.off[w];
+        rl.meta[q] = make_int2(p, ro);
+        fill_tiles(rl.tile, eo, len, (int)q);
+    }
+}
+
+// Delete, top-down alternative to the pointer jumping of Algorithm 1 (same
+// representatives): the detached vertices are the cut vertices and every
+// descendant of one in the cut forest, and a detached vertex's piece is the
+// nearest cut vertex above it.  A level-synchronous search goes down from
+// the cut vertices over tree children (neighbours w of v with parent[w] ==
+// v, found in v's row or, for edges held outside the rows, in the overflow
+// list) and touches only the detached vertices' rows, where pointer jumping
+// touches every vertex of every cut tree.  Each level's rows are appended to
+// the row list of the cross-edge scan as they are found (rows and entry
+// ranges from one packed counter, 32-entry tiles), so level k reads exactly
+// the rows appended in level k-1 with the tile-window scan of k_scan_lb, and
+// the scan afterwards reuses the list (the piece left out of every tree is
+// its root piece).  Every level appends through counters of its own (a ring
+// of three: level k appends to slot k+1, reads the final count of slot k
+// after the barrier and clears slot k+2), so all blocks see the same level
+// sizes although some append while others still read.  New representatives
+// go to J1 and are committed only when the search ends within its budget
+// (vertices, entries, levels); otherwise nothing is published and the
+// pointer-jumping path runs.
+__global__ void __launch_bounds__(BLK, 4)
+    k_detach(Ctl *ctl, const int *cuts, const int *par, int *rep, Csr g, const u64 *ovf, u64 ovf_cap, RowList rl,
+             int *A, int *J1, unsigned *det_ep, unsigned *det_claim, const int *rold, long long budget_v,
+             long long budget_e, int max_levels, int *oc, int *op) {
+    if (*(volatile int *)&ctl->skip) return;
+    const unsigned ep = ctl->epoch;
+    const long long nc = (long long)ctl->ncut;
+    u64 *bar = &ctl->bar[6];
+    const int lane = threadIdx.x & 31;
+    // level 0: the cut vertices (pieces of their own), slot 0
+    for (long long b0 = gtid() & ~31ll; b0 < nc; b0 += gstride()) {
+        const long long i = b0 + lane;
+        const bool on = i < nc;
+        int c = 0, len = 0, ro = 0;
+        if (on) {
+            c = cuts[i];
+            ro = rold[c];
+            J1[c] = c;
+            __threadfence();   // J1 before the stamp that publishes it
+            det_ep[c] = ep;
+            len = min(g.used[c], (int)(g.off[c + 1] - g.off[c]));
+        }
+        warp_detach_append(&ctl->dv[0], &ctl->dp[0], 0, 0, rl, A, g, on, c, len, c, ro);
+    }
+    // the tree edges held outside the rows (overflow list), as (child,
+    // parent): listed once, read by every level (few: edges land there
+    // only when a row is full)
+    {
+        const long long no = (long long)min((u64)ctl->ovf_count, ovf_cap);
+        for (long long b0 = gtid() & ~31ll; b0 < no; b0 += gstride()) {
+            const long long i = b0 + lane;
+            int cw = -1, pv = -1;
+            if (i < no) {
+                const u64 k = ovf[i];
+                if (k != TOMB_KEY) {
+                    const int a = (int)klo(k), b = (int)khi(k);
+                    if (LD(par[a]) == b) cw = a, pv = b;
+                    else if (LD(par[b]) == a) cw = b, pv = a;
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, cw >= 0);
+            if (!m) continue;
+            const int ld = __ffs(m) - 1;
+            u64 q0 = 0;
+            if (lane == ld) q0 = atomicAdd(&ctl->dovf, (u64)__popc(m));
+            q0 = __shfl_sync(0xffffffffu, q0, ld);
+            if (cw >= 0) {
+                const u64 q = q0 + __popc(m & ((1u << lane) - 1u));
+                oc[q] = cw;
+                op[q] = pv;
+            }
+        }
+    }
+    long long vb = 0;   // vertices listed before the current level's
+    u64 pb = 0;         // rows << 32 | entries listed before it
+    int lvl = 0;
+    bool ok = true;
+    for (;; ++lvl) {
+        if (!grid_barrier(ctl, bar)) return;
+        // the level found in the last round (slot lvl % 3) is final
+        const int sl = lvl % 3, sn = (lvl + 1) % 3;
+        const long long dv = (long long)*(volatile u64 *)&ctl->dv[sl];
+        const u64 dp = *(volatile u64 *)&ctl->dp[sl];
+        if (gtid() == 0) ctl->dv[(lvl + 2) % 3] = ctl->dp[(lvl + 2) % 3] = 0;   // read last one level ago
+        const unsigned e_lo = (unsigned)pb, r_lo = (unsigned)(pb >> 32);
+        const long long vn = vb + dv;
+        const u64 pn = pb + dp;
+        const unsigned e_hi = (unsigned)pn, r_hi = (unsigned)(pn >> 32);
+        if (dv == 0) break;   // the last level found nothing
+        if (lvl >= max_levels || vn > budget_v || (long long)e_hi > budget_e) {
+            ok = false;
+            break;
+        }
+        (void)r_lo;
+        // tiles covering the entries of the rows found in the last level,
+        // a contiguous range of tiles per warp
+        const unsigned T0 = e_lo >> 5, T1 = (e_hi + 31) >> 5;
+        const unsigned NT = T1 - T0;
+        const unsigned nw = (unsigned)(gstride() >> 5), wid = (unsigned)(gtid() >> 5);
+        const unsigned per = (NT + nw - 1) / nw;
+        for (unsigned it = 0; it < per; ++it) {
+            const unsigned T = T0 + wid * per + it;
+            bool child = false;
+            int w = -1, p = 0, ro = 0;
+            if (T < T1) {   // warp-uniform
+                const unsigned t0 = T << 5;
+                // (rows of earlier levels, written by other blocks: read through L2)
+                const int r0 = LD(rl.tile[T]);
+                const unsigned wr = (unsigned)r0 + lane;
+                const bool wok = wr < r_hi;
+                const unsigned wo = wok ? LD(rl.roff[wr]) : 0xFFFFFFFFu;
+                const int wv = wok ? LD(rl.D[wr]) : 0;
+                const unsigned wb = wok ? LD(rl.base[wr]) : 0;
+                const int2 wm = wok ? __ldcg(&rl.meta[wr]) : make_int2(0, 0);
+                const unsigned pos = wo - t0;
+                const unsigned bit = (lane > 0 && pos < 32) ? (1u << pos) : 0u;
+                const unsigned starts = __reduce_or_sync(0xffffffffu, bit);
+                const int c = __popc(starts & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u)));
+                const unsigned rstart = __shfl_sync(0xffffffffu, wo, c);
+                const int v = __shfl_sync(0xffffffffu, wv, c);
+                const unsigned rb = __shfl_sync(0xffffffffu, wb, c);
+                p = __shfl_sync(0xffffffffu, wm.x, c);
+                ro = __shfl_sync(0xffffffffu, wm.y, c);
+                const unsigned e = t0 + lane;
+                if (e >= e_lo && e < e_hi) {
+                    w = __ldcs(&g.col[(size_t)(rb + (e - rstart))]);
+                    child = w >= 0 && LD(par[w]) == v;
+                }
+            }
+            int len = 0;
+            if (child) {
+                J1[w] = p;
+                __threadfence();
+                det_ep[w] = ep;
+                len = min(g.used[w], (int)(g.off[w + 1] - g.off[w]));
+            }
+            warp_detach_append(&ctl->dv[sn], &ctl->dp[sn], vn, pn, rl, A, g, child, w, len, p, ro);
+        }
+        // children joined by a tree edge outside the rows: a vertex whose
+        // parent is detached (published: its J1 before its stamp)
+        const long long nt = (long long)*(volatile u64 *)&ctl->dovf;
+        for (long long b0 = gtid() & ~31ll; b0 < nt; b0 += gstride()) {
+            const long long i = b0 + lane;
+            bool child = false;
+            int w = -1, p = 0, ro = 0, len = 0;
+            if (i < nt) {
+                const int cw = LD(oc[i]), pv = LD(op[i]);
+                const bool pd = LD(det_ep[pv]) == ep;
+                __threadfence();
+                if (pd && LD(det_claim[cw]) != ep && atomicExch(&det_claim[cw], ep) != ep) {
+                    child = true;
+                    w = cw;
+                    p = LD(J1[pv]);
+                    ro = rep[w];   // rep still holds the old roots
+                }
+            }
+            if (child) {
+                J1[w] = p;
+                __threadfence();
+                det_ep[w] = ep;
+                len = min(g.used[w], (int)(g.off[w + 1] - g.off[w]));
+            }
+            warp_detach_append(&ctl->dv[sn], &ctl->dp[sn], vn, pn, rl, A, g, child, w, len, p, ro);
+        }
+        vb = vn;
+        pb = pn;
+    }
+    // over budget: nothing was published (naff, ndet and rep untouched);
+    // the pointer-jumping path takes over from the cut
+    if (!ok) {
+        if (gtid() == 0) ctl->det_levels = -lvl;
+        return;
+    }
+    // commit the representatives of the detached vertices
+    for (long long i = gtid(); i < vb; i += gstride()) {
+        const int v = A[i];
+        rep[v] = LD(J1[v]);
+    }
+    if (gtid() == 0) {
+        ctl->naff = (u64)vb;
+        ctl->ndet = pb >> 32;
+        ctl->det_entries = (long long)(pb & 0xFFFFFFFFull);
+        rl.roff[pb >> 32] = (unsigned)pb;
+        ctl->det_levels = lvl;
+        ctl->td = 1;
+    }
+}
+
+// After the orientation of a top-down delete: does some cut tree's root
+// piece get a new representative (a detached piece with a smaller root id
+// joined its super-tree)?  Then its vertices must be listed for the refresh
+// and the path marks (k_aff_collect with roots_only).
+__global__ void k_rootcheck(Ctl *ctl, const int *cuts, const int *rold, const unsigned *rep_ep) {
+    if (*(volatile int *)&ctl->skip || !*(volatile int *)&ctl->td) return;
+    const unsigned ep = ctl->epoch;
+    const long long nc = (long long)ctl->ncut;
+    for (long long i = gtid(); i < nc; i += gstride())
+        if (rep_ep[rold[cuts[i]]] == ep) ctl->need_root = 1;
+}
+
 // Representatives (Algorithm 1, parallel pointer jumping) of the listed
 // vertices: rep[v] = root of v in F^ (J starts as a copy of parent).
 // Delete mode (1) then chooses the rows to scan for cross edges: every cross
@@ -255,6 +513,7 @@ __global__ void __launch_bounds__(BLK, 6)
     int *const D = rl.D;
     unsigned *const roff = rl.roff;
     if (*(volatile int *)&ctl->skip) return;
+    if (mode == 1 && *(volatile int *)&ctl->td) return;   // the top-down search found the pieces
     long long cnt = use_list ? (long long)ctl->naff : cnt_static;
     if constexpr (sync_rounds != 0) {
         // synchronous doubling J <- J o J (ping-pong).  A pointer that has
@@ -1148,11 +1407,28 @@ cudaError_t launch_begin(Ctl *ctl, int op, long long len, const int *batch, cuda
     return cudaGetLastError();
 }
 cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, int *A, int *rold,
-                               unsigned *w, u64 *heavy, Ctl *ctl, const int *par, int *J, cudaStream_t s) {
-    k_aff_collect<<<d.grid_pass, BLK, 0, s>>>(n, rep, aff_ep, A, rold, w, heavy, ctl, par, J);
+                               unsigned *w, u64 *heavy, Ctl *ctl, const int *par, int *J, int roots_only,
+                               cudaStream_t s) {
+    k_aff_collect<<<d.grid_pass, BLK, 0, s>>>(n, rep, aff_ep, A, rold, w, heavy, ctl, par, J, roots_only);
     (void)d;
     return cudaGetLastError();
 }
+cudaError_t launch_detach(const Dev &d, Ctl *ctl, const int *cuts, const int *par, int *rep, Csr g, const u64 *ovf,
+                          u64 ovf_cap, RowList rl, int *A, int *J1, unsigned *det_ep, unsigned *det_claim,
+                          const int *rold, long long budget_v, long long budget_e, int max_levels, int *oc, int *op,
+                          cudaStream_t s) {
+    void *args[] = {(void *)&ctl,     (void *)&cuts,     (void *)&par,      (void *)&rep,        (void *)&g,
+                    (void *)&ovf,     (void *)&ovf_cap,  (void *)&rl,       (void *)&A,          (void *)&J1,
+                    (void *)&det_ep,  (void *)&det_claim, (void *)&rold,    (void *)&budget_v,   (void *)&budget_e,
+                    (void *)&max_levels, (void *)&oc,    (void *)&op};
+    return cudaLaunchCooperativeKernel((const void *)k_detach, d.coop_detach, BLK, args, 0, s);
+}
+cudaError_t launch_rootcheck(const Dev &d, Ctl *ctl, const int *cuts, const int *rold, const unsigned *rep_ep,
+                             cudaStream_t s) {
+    k_rootcheck<<<d.nsm, BLK, 0, s>>>(ctl, cuts, rold, rep_ep);
+    return cudaGetLastError();
+}
+unsigned coop_blocks_detach(int nsm) { return coop_blocks((const void *)k_detach, nsm, 4); }
 cudaError_t launch_jump_async(const Dev &d, const int *A, Ctl *ctl, int *J, int *X, int *Y, cudaStream_t s) {
     k_jump_async<<<d.coop_jump, BLK, 0, s>>>(A, ctl, J, X, Y);
     return cudaGetLastError();

@@ -270,7 +270,7 @@ __global__ void k_ins_place(const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, 
 // orientation).  The old root of a cut tree is stamped "affected"; the cut
 // vertex becomes a piece root and is stamped in cut_ep.
 __global__ void k_del_claim(Index ix, Csr g, u64 *ovf, int *parent, const int *rep, Ctl *ctl, unsigned *aff_ep,
-                            unsigned *cut_ep, int *cutlist, unsigned *w) {
+                            unsigned *cut_ep, int *cutlist, unsigned *w, int *rold) {
     if (*(volatile int *)&ctl->skip) return;
     const int *batch = ctl->batch;
     const long long len = ctl->batch_len;
@@ -310,7 +310,8 @@ __global__ void k_del_claim(Index ix, Csr g, u64 *ovf, int *parent, const int *r
                     if (c >= 0) {
                         parent[c] = c;
                         cut_ep[c] = ep;
-                        w[c] = 0;   // c roots a new piece: its weight slot
+                        w[c] = 0;     // c roots a new piece: its weight slot
+                        rold[c] = rc; // and the old root of its tree
                     }
                 }
                 wins += won;
@@ -639,8 +640,9 @@ cudaError_t launch_ins_place(const Dev &d, const u64 *nkey, const u64 *nslot, Ct
     return cudaGetLastError();
 }
 cudaError_t launch_del_claim(long long len, Index ix, Csr g, u64 *ovf, int *parent, const int *rep, Ctl *ctl,
-                             unsigned *aff_ep, unsigned *cut_ep, int *cutlist, unsigned *w, cudaStream_t s) {
-    k_del_claim<<<gsz(len), BLK, 0, s>>>(ix, g, ovf, parent, rep, ctl, aff_ep, cut_ep, cutlist, w);
+                             unsigned *aff_ep, unsigned *cut_ep, int *cutlist, unsigned *w, int *rold,
+                             cudaStream_t s) {
+    k_del_claim<<<gsz(len), BLK, 0, s>>>(ix, g, ovf, parent, rep, ctl, aff_ep, cut_ep, cutlist, w, rold);
     return cudaGetLastError();
 }
 cudaError_t launch_scan_rows(const Dev &d, RowList rl, Ctl *ctl, Csr g, const int *rep, bool sg, PairTable pt,

@@ -16,6 +16,7 @@ struct Dev {
     unsigned coop_mark;
     unsigned coop_bfs;
     unsigned coop_et;
+    unsigned coop_detach;
     unsigned grid_scan;   // row scan: the co-resident block count
     unsigned grid_pass;   // vertex passes (affected list, refresh): the co-resident block count
 };
@@ -34,7 +35,8 @@ cudaError_t launch_validate_batch(long long len, int n, Ctl *ctl, cudaStream_t s
 cudaError_t launch_ins_claim(long long len, Index ix, Ctl *ctl, u64 *nkey, u64 *nslot, cudaStream_t s);
 
 cudaError_t launch_del_claim(long long len, Index ix, Csr g, u64 *ovf, int *parent, const int *rep, Ctl *ctl,
-                             unsigned *aff_ep, unsigned *cut_ep, int *cutlist, unsigned *w, cudaStream_t s);
+                             unsigned *aff_ep, unsigned *cut_ep, int *cutlist, unsigned *w, int *rold,
+                             cudaStream_t s);
 // The rows a delete batch scans for cross edges, one entry per listed
 // vertex u: u itself, the exclusive prefix sum of the row lengths (roff[nd]
 // = total), the row's start in the CSR, and (rep[u], piece left out of the
@@ -71,7 +73,17 @@ cudaError_t launch_check_cross(const int *pairs, long long m, const int *rep, in
 // forest.cu ------------------------------------------------------------
 cudaError_t launch_begin(Ctl *ctl, int op, long long len, const int *batch, cudaStream_t s);
 cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsigned *aff_ep, int *A, int *rold,
-                               unsigned *w, u64 *heavy, Ctl *ctl, const int *par, int *J, cudaStream_t s);
+                               unsigned *w, u64 *heavy, Ctl *ctl, const int *par, int *J, int roots_only,
+                               cudaStream_t s);
+// delete: detached vertices top-down from the cut vertices (falls back to
+// the pointer jumping above when over budget); root pieces to list after it
+cudaError_t launch_detach(const Dev &d, Ctl *ctl, const int *cuts, const int *par, int *rep, Csr g, const u64 *ovf,
+                          u64 ovf_cap, RowList rl, int *A, int *J1, unsigned *det_ep, unsigned *det_claim,
+                          const int *rold, long long budget_v, long long budget_e, int max_levels, int *oc, int *op,
+                          cudaStream_t s);
+cudaError_t launch_rootcheck(const Dev &d, Ctl *ctl, const int *cuts, const int *rold, const unsigned *rep_ep,
+                             cudaStream_t s);
+unsigned coop_blocks_detach(int nsm);
 cudaError_t launch_jump_async(const Dev &d, const int *A, Ctl *ctl, int *J, int *X, int *Y, cudaStream_t s);
 cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, const int *par,
                         int *J, int *J1, int *rep, RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy,

@@ -64,6 +64,7 @@ def test_root_search_variants(variant, monkeypatch):
     rounds, path-halving walks) give the oracle's forest too; R-MAT-16 and a
     deep grid (long doubling chains)."""
     monkeypatch.setenv("DRSF_JUMP", variant)
+    monkeypatch.setenv("DRSF_DETACH", "0")   # root search for every delete (no top-down search first)
     g = workloads.rmat_graph(16, 16, seed=2)
     run_trajectory(g, [(I, 1000), (D, 1000), (I, 10_000), (D, 10_000)] * 2, seed=3)
     g = workloads.grid_graph(256, 256, seed=3)
@@ -244,3 +245,33 @@ def test_direct_launches_without_captured_graphs(monkeypatch):
     for env in ("0", "1"):
         monkeypatch.setenv("DRSF_GRAPHS", env)
         run_trajectory(g, [(I, 1000), (D, 1000), (I, 60_000), (D, 10_000), (I, 200_000), (D, 50_000)], seed=3)
+
+
+def test_top_down_detach_and_its_fallback(monkeypatch):
+    """Deletes look for their detached vertices top-down from the cut
+    vertices first and hand over to pointer jumping when that search runs
+    over its budget (here: the level limit on a deep grid).  Both paths give
+    the oracle's forests; the counters show which one each batch took; and
+    with DRSF_DETACH=0 the same trajectories match too."""
+    seen = {"top": 0, "fallback": 0}
+
+    def watch(g, schedule, seed, **kw):
+        f = make_forest(g)
+        keys, par = g.keys, g.parent
+        tr = workloads.Trajectory(g, seed, tree_frac=kw.get("tree_frac", 0.5), local=kw.get("local", 0))
+        try:
+            for op, b in schedule:
+                batch = tr.next_batch(op, b)
+                keys, par, st = check_batch(f, g.n, keys, par, op, batch)
+                tr.advance(batch, op, par)
+                if op == D and st["tree_cut"] > 0:
+                    seen["top" if st["detach_levels"] > 0 else "fallback"] += 1
+        finally:
+            f.close()
+
+    watch(workloads.rmat_graph(16, 16, seed=2), [(I, 1000), (D, 1000), (I, 10_000), (D, 10_000)] * 2, seed=3)
+    watch(workloads.grid_graph(1024, 1024, seed=3), [(D, 20_000), (I, 20_000)] * 2, seed=4, tree_frac=0.9,
+          local=64)
+    assert seen["top"] > 0 and seen["fallback"] > 0, seen
+    monkeypatch.setenv("DRSF_DETACH", "0")
+    run_trajectory(workloads.rmat_graph(16, 16, seed=2), [(I, 1000), (D, 1000), (I, 10_000), (D, 10_000)], seed=3)
