@@ -402,7 +402,7 @@ def run_ours(args, rank, ws, local):
     batch_stats = {oname: {key: _mean(op, key) for key in (
         "applied", "tree_cut", "affected", "detached", "scanned", "candidates", "hook_rounds", "replacement",
         "rank_rounds", "active", "reversed", "mark_rounds", "jump_rounds", "jump_visits", "detach_levels",
-        "detach_entries")} for op, oname in ((0, "insert"),
+        "detach_entries", "core_arcs")} for op, oname in ((0, "insert"),
                                                                                         (1, "delete"))}
 
     # end to end through the C ABI with host buffers

@@ -154,6 +154,9 @@ typedef struct {
                               detached vertices (0: none, negative: it ran
                               over its budget and pointer jumping took over) */
     int64_t detach_entries;/* delete: adjacency entries that search read */
+    int64_t core_arcs;     /* arcs of the super-forest core that the Euler
+                              tour ranked (pieces with one replacement edge
+                              are oriented without it) */
 } drsf_batch_stats;
 
 /* Allocator hooks.  alloc(bytes, stream, ctx) returns device memory or NULL;

@@ -48,7 +48,7 @@ class BatchStats(ctypes.Structure):
         "batch_len", "self_loops", "dropped", "applied", "tree_cut", "affected", "detached", "scanned",
         "candidates", "hook_rounds", "replacement", "rank_rounds", "active", "reversed", "mark_rounds",
         "jump_rounds", "edges", "overflow", "rebuilds", "jump_visits", "supergraph", "detach_levels",
-        "detach_entries")]
+        "detach_entries", "core_arcs")]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

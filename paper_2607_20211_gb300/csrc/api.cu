@@ -755,6 +755,9 @@ static drsf_status launch_rest(drsf_ctx *h, int op, bool sg, long long glen, cud
     oa.ep = h->oep;
     oa.eid = h->oeid;
     oa.eroot = h->oeroot;
+    oa.cel = h->nx1;   // (the grid ranking's second buffer: unused on the one-block path)
+    oa.parent = h->parent;
+    oa.n = h->n;
     prof_begin(h, PH_ORIENT, s);
     CK(launch_orient(h->dev, ctl, oa, s));
     prof_end(h, PH_ORIENT, 1, s);
@@ -1244,6 +1247,7 @@ drsf_status drsf_stats(drsf_handle h, drsf_batch_stats *out, drsf_stream stream)
     out->supergraph = h->last_sg;
     out->detach_levels = c.det_levels;
     out->detach_entries = c.det_entries;
+    out->core_arcs = (int64_t)c.ncore;
     return latched(h);
 }
 

@@ -21,28 +21,42 @@
 #define ORIENT_SMEM_ARCS 12288
 #define ORIENT_SMEM_BYTES (4 * ORIENT_SMEM_ARCS * (int)sizeof(int))
 #define ORIENT_THREADS 1024
+// a core of at most this many edges is oriented by one block (measured on
+// R-MAT-22: faster than the grid phases for small batches' cores of tens of
+// edges, slower for the 100K batches' cores of about 900 edges)
+#define ORIENT_SMALL_EDGES 256
 // independent items per thread and iteration in the pointer-doubling rounds
 #define JU 4
 // the same for the final pass of the jump (more state per item)
 #define JF 2
-// consecutive items per thread in the list-building vertex passes
+// consecutive items per thread in the list-building vertex passes: IPT over
+// a list, IPN over all n vertices (more loads in flight per thread: those
+// passes are one dependent gather behind a streaming load)
 #define IPT 4
+#define IPN 16
 // longest path reversed by one walking thread (longer ones: doubling marks)
 #define WALK_MAX 64
 
-// x[k] = a[i0 + k] for k < IPT (i0 a multiple of IPT; a 16-byte aligned):
-// one vector load when all IPT items are in range.
-__device__ __forceinline__ void load_ipt(const int *a, long long i0, long long cnt, int x[IPT]) {
-    if (i0 + IPT <= cnt) {
-        int4 q = *reinterpret_cast<const int4 *>(a + i0);
-        x[0] = q.x;
-        x[1] = q.y;
-        x[2] = q.z;
-        x[3] = q.w;
+// x[k] = a[i0 + k] for k < IP (IP a multiple of 4, i0 a multiple of IP, a
+// 16-byte aligned): vector loads when all IP items are in range.
+template <int IP>
+__device__ __forceinline__ void load_vec(const int *a, long long i0, long long cnt, int (&x)[IP]) {
+    if (i0 + IP <= cnt) {
+#pragma unroll
+        for (int j = 0; j < IP / 4; ++j) {
+            const int4 q = *reinterpret_cast<const int4 *>(a + i0 + 4 * j);
+            x[4 * j] = q.x;
+            x[4 * j + 1] = q.y;
+            x[4 * j + 2] = q.z;
+            x[4 * j + 3] = q.w;
+        }
     } else {
 #pragma unroll
-        for (int k = 0; k < IPT; ++k) x[k] = i0 + k < cnt ? a[i0 + k] : 0;
+        for (int k = 0; k < IP; ++k) x[k] = i0 + k < cnt ? a[i0 + k] : 0;
     }
+}
+__device__ __forceinline__ void load_ipt(const int *a, long long i0, long long cnt, int (&x)[IPT]) {
+    load_vec<IPT>(a, i0, cnt, x);
 }
 // a detached piece is left out of the cross-edge scan instead of its tree's
 // root piece only if it has this many more vertices (the swap costs a full
@@ -91,45 +105,61 @@ __global__ void k_begin(Ctl *ctl, int op, long long len, const int *batch) {
 
 // Delete: list the vertices of every tree that lost a tree edge (its old
 // root was stamped by the cut), with their old root.
-// Each thread takes IPT consecutive vertices per iteration (one vector load
-// of rep, IPT gathers in flight) and the block reserves its list slots with
-// one atomic; the list stays in vertex order.
+// Each thread takes IPN vertices per iteration, k-major (item k of thread t
+// is vertex b0 + k * blockDim + t, so every load and store of a warp covers
+// 32 consecutive vertices), with all IPN loads and gathers in flight before
+// any is used.  A warp's listed vertices take consecutive slots (one block
+// reservation of the warps' totals), in vertex order within the warp.
 // With roots_only (after a top-down search of the detached vertices, when
 // some tree's root piece is re-rooted) only the root pieces' vertices are
 // appended (the detached ones already hold their new representative, which
 // is no stamped old root); otherwise the pass runs only when the top-down
 // search did not (the pointer-jumping path).
-__global__ void k_aff_collect(int n, const int *rep, const unsigned *aff_ep, int *A, int *rold, unsigned *w,
-                              u64 *heavy, Ctl *ctl, const int *par, int *J, int roots_only) {
+__global__ void __launch_bounds__(BLK) k_aff_collect(int n, const int *rep, const unsigned *aff_ep, int *A, int *rold,
+                                                     unsigned *w, u64 *heavy, Ctl *ctl, const int *par, int *J,
+                                                     int roots_only) {
+    static_assert(IPN <= 32, "item masks are 32 bits");
     if (*(volatile int *)&ctl->skip) return;
     if (roots_only ? !(*(volatile int *)&ctl->td && *(volatile int *)&ctl->need_root) : *(volatile int *)&ctl->td)
         return;
     unsigned ep = ctl->epoch;
-    const long long step = (long long)gridDim.x * blockDim.x * IPT;
-    for (long long b0 = (long long)blockIdx.x * blockDim.x * IPT; b0 < n; b0 += step) {
-        const long long v0 = b0 + (long long)threadIdx.x * IPT;
-        int r[IPT];
-        bool in[IPT];
-        load_ipt(rep, v0, n, r);
-        int c = 0;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const long long step = (long long)gridDim.x * blockDim.x * IPN;
+    for (long long b0 = (long long)blockIdx.x * blockDim.x * IPN; b0 < n; b0 += step) {
+        const long long v0 = b0 + threadIdx.x;
+        int r[IPN];
 #pragma unroll
-        for (int k = 0; k < IPT; ++k) {
-            in[k] = v0 + k < n && aff_ep[r[k]] == ep;
-            c += in[k];
+        for (int k = 0; k < IPN; ++k) {
+            const long long v = v0 + (long long)k * blockDim.x;
+            r[k] = v < n ? rep[v] : 0;
         }
-        long long p = block_reserve(&ctl->naff, c);
+        unsigned in = 0;
 #pragma unroll
-        for (int k = 0; k < IPT; ++k) {
-            if (!in[k]) continue;
-            const int v = (int)(v0 + k);
-            A[p++] = v;
-            if (roots_only) continue;
-            rold[v] = r[k];
-            if (J) J[v] = par[v];   // seed of the asynchronous doubling
-            if (r[k] == v) {   // the old root: piece-weight and heaviest-piece slots
-                w[v] = 0;
-                heavy[v] = 0;
+        for (int k = 0; k < IPN; ++k) {
+            const long long v = v0 + (long long)k * blockDim.x;
+            if (v < n && aff_ep[r[k]] == ep) in |= 1u << k;
+        }
+        // (the warp's ballots are recomputed below rather than kept)
+        const int tot = __reduce_add_sync(0xffffffffu, __popc(in));
+        long long p = block_reserve(&ctl->naff, lane == 0 ? tot : 0);
+        p = __shfl_sync(0xffffffffu, p, 0);
+#pragma unroll
+        for (int k = 0; k < IPN; ++k) {
+            const unsigned bk = __ballot_sync(0xffffffffu, (in >> k) & 1u);
+            if ((in >> k) & 1u) {
+                const int v = (int)(v0 + (long long)k * blockDim.x);
+                A[p + __popc(bk & lt)] = v;
+                if (!roots_only) {
+                    rold[v] = r[k];
+                    if (J) J[v] = par[v];   // seed of the asynchronous doubling
+                    if (r[k] == v) {        // the old root: piece-weight and heaviest-piece slots
+                        w[v] = 0;
+                        heavy[v] = 0;
+                    }
+                }
             }
+            p += __popc(bk);
         }
     }
 }
@@ -168,9 +198,26 @@ __device__ __forceinline__ void piece_count(int *s_wk, unsigned *s_wc, unsigned 
 }
 
 // tile[T] = row for the tiles of 32 entries whose first entry lies in the
-// row of entries [st, st + d), d > 0 (rows are never empty)
-__device__ __noinline__ void fill_tiles(int *tile, long long st, long long d, int row) {
-    for (long long T = (st + 31) >> 5; T <= (st + d - 1) >> 5; ++T) tile[T] = row;
+// row of entries [st, st + d), d > 0 (rows are never empty), for the rows of
+// the lanes with `on` (called by the whole warp).  A lane writes the tiles of
+// a short row itself; a long row (a hub's, up to tens of thousands of tiles)
+// is written by the whole warp, so no lane writes more than a few tiles of
+// it in sequence.
+#define FILL_OWN 4
+__device__ __forceinline__ void warp_fill_tiles(int *tile, bool on, long long st, long long d, int row) {
+    const int lane = threadIdx.x & 31;
+    const long long t0 = (st + 31) >> 5, t1 = on ? ((st + d - 1) >> 5) + 1 : t0;   // tiles [t0, t1)
+    const bool big = t1 - t0 > FILL_OWN;
+    if (on && !big)
+        for (long long T = t0; T < t1; ++T) tile[T] = row;
+    unsigned bm = __ballot_sync(0xffffffffu, big);
+    while (bm) {
+        const int l = __ffs(bm) - 1;
+        bm &= bm - 1;
+        const long long a = __shfl_sync(0xffffffffu, t0, l), b = __shfl_sync(0xffffffffu, t1, l);
+        const int r = __shfl_sync(0xffffffffu, row, l);
+        for (long long T = a + lane; T < b; T += 32) tile[T] = r;
+    }
 }
 
 // Representatives by asynchronous pointer doubling in place (delete batches
@@ -284,15 +331,15 @@ __device__ __forceinline__ void warp_detach_append(u64 *vc, u64 *pc, long long v
     u64 base = 0;
     if (lane == fl) base = atomicAdd(pc, ((u64)__popc(fm) << 32) | (u64)(unsigned)tot);
     base = __shfl_sync(0xffffffffu, base, fl) + pb;
+    const long long q = (long long)(base >> 32) + __popc(fm & lt);
+    const long long eo = (long long)(base & 0xFFFFFFFFull) + ex;
     if (f) {
-        const long long q = (long long)(base >> 32) + __popc(fm & lt);
-        const long long eo = (long long)(base & 0xFFFFFFFFull) + ex;
         rl.D[q] = w;
         rl.roff[q] = (unsigned)eo;
         rl.base[q] = (unsigned)g.off[w];
         rl.meta[q] = make_int2(p, ro);
-        fill_tiles(rl.tile, eo, len, (int)q);
     }
+    warp_fill_tiles(rl.tile, f, eo, len, (int)q);
 }
 
 // Delete, top-down alternative to the pointer jumping of Algorithm 1 (same
@@ -656,14 +703,15 @@ __global__ void __launch_bounds__(BLK, 6)
             long long q[JF], eo[JF];
             block_reserve_rows<JF>(&ctl->ndet, scan, len, q, eo);
 #pragma unroll
-            for (int k = 0; k < JF; ++k)
+            for (int k = 0; k < JF; ++k) {
                 if (scan[k]) {
                     D[q[k]] = v[k];
                     roff[q[k]] = (unsigned)eo[k];
                     rl.base[q[k]] = (unsigned)g.off[v[k]];
                     rl.meta[q[k]] = make_int2(p[k], ro[k]);
-                    fill_tiles(rl.tile, eo[k], len[k], (int)q[k]);
                 }
+                warp_fill_tiles(rl.tile, scan[k], eo[k], len[k], (int)q[k]);
+            }
         }
         __syncthreads();
         for (int t = threadIdx.x; t < WT_SLOTS; t += blockDim.x)
@@ -747,8 +795,8 @@ __global__ void __launch_bounds__(BLK, 6)
                 roff[q[0]] = (unsigned)eo[0];
                 rl.base[q[0]] = (unsigned)g.off[v];
                 rl.meta[q[0]] = make_int2(pv, hp);
-                fill_tiles(rl.tile, eo[0], len[0], (int)q[0]);
             }
+            warp_fill_tiles(rl.tile, scan[0], eo[0], len[0], (int)q[0]);
         }
         if (!grid_barrier(ctl, &ctl->bar[0])) return;
     }
@@ -938,6 +986,115 @@ __global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int 
     if (gtid() == 0) ctl->hook_rounds = r;
 }
 
+// Orientation of replacement edge i: down = its lower-id endpoint's piece
+// p0 is the parent of the other piece p1.  The child piece P of edge {x, y}
+// (x in P) gets the oriented edge x -> y, its attach point x and the
+// super-tree's root as its new representative (each non-root piece is the
+// child of exactly one edge: one write per piece; the super-root keeps its
+// representative).
+__device__ __forceinline__ void orient_one(const OrientArgs &a, long long i, bool down, unsigned ep) {
+    const u64 k = a.er[i];
+    const int x0 = (int)klo(k), x1 = (int)khi(k);
+    const int p0 = LD(a.ep[2 * i]), p1 = LD(a.ep[2 * i + 1]);
+    const int child = down ? p1 : p0;
+    const int x = down ? x1 : x0, y = down ? x0 : x1;
+    a.chx[i] = x;
+    a.chy[i] = y;
+    a.att_x[child] = x;
+    a.att_ep[child] = ep;
+    a.newrep[child] = LD(a.minp[LD(a.eroot[i])]);
+    a.rep_ep[child] = ep;
+}
+
+// Wyllie list ranking of ncore list cells in shared memory by one block:
+// val (svc) = cells from here to the end of the list, next pointers in snc
+// (NIL at the end); svn / snn are the ping-pong buffers.  Returns the rounds
+// taken (ERR_ROUNDS latched if the bound is hit) and leaves the ranks in
+// *out (one of svc / svn).
+__device__ int rank_block(Ctl *ctl, int *svc, int *svn, int *snc, int *snn, int ncore, int **out) {
+    int r = 0;
+    for (;; ++r) {
+        int ch = 0;
+        for (int i = threadIdx.x; i < ncore; i += blockDim.x) {
+            const int sx = snc[i];
+            if (sx != NIL) {
+                svn[i] = svc[i] + svc[sx];
+                snn[i] = snc[sx];
+                ch = 1;
+            } else {
+                svn[i] = svc[i];
+                snn[i] = NIL;
+            }
+        }
+        const int any = __syncthreads_or(ch);
+        int *t = svc; svc = svn; svn = t;
+        t = snc; snc = snn; snn = t;
+        if (!any) break;
+        if (r >= MAX_ROUNDS) {
+            if (threadIdx.x == 0) atomicOr(&ctl->err, ERR_ROUNDS);
+            break;
+        }
+    }
+    *out = svc;
+    return r + 1;
+}
+
+// The core of the super-forest (the edges that are not leaf edges, listed
+// in cel) oriented by one block: adjacency ranges claimed by the first arc
+// of each core piece, arcs placed, Euler successors (as in the grid phases
+// of k_orient) written straight into shared memory, ranked there, and each
+// core edge oriented by its arc that comes first.  Block barriers only.
+__device__ void orient_small_core(Ctl *ctl, const OrientArgs &a, long long nce, unsigned ep) {
+    __shared__ int s_nc;
+    if (threadIdx.x == 0) s_nc = 0;
+    __syncthreads();
+    for (long long t = threadIdx.x; t < 2 * nce; t += blockDim.x) {
+        const long long j = 2 * (long long)LD(a.cel[t >> 1]) + (t & 1);
+        const int id = LD(a.eid[j]);
+        if (atomicCAS(&a.poff[id], -1, -2) == -1) a.poff[id] = atomicAdd(&s_nc, LD(a.cdeg[id]));
+    }
+    __syncthreads();
+    const int ncore = s_nc;
+    for (long long t = threadIdx.x; t < 2 * nce; t += blockDim.x) {
+        const long long j = 2 * (long long)LD(a.cel[t >> 1]) + (t & 1);
+        const int id = LD(a.eid[j]);
+        const int slot = a.poff[id] + atomicAdd(&a.pcur[id], 1);
+        a.adj[slot] = (int)j;
+        a.apos[j] = slot;
+    }
+    __syncthreads();
+    extern __shared__ int s_rank[];
+    int *svc = s_rank, *svn = svc + ORIENT_SMEM_ARCS, *snc = svn + ORIENT_SMEM_ARCS, *snn = snc + ORIENT_SMEM_ARCS;
+    for (long long t = threadIdx.x; t < 2 * nce; t += blockDim.x) {
+        const long long j = 2 * (long long)LD(a.cel[t >> 1]) + (t & 1);
+        const long long tw = j ^ 1;
+        const int hid = LD(a.eid[tw]);   // the arc's head = the twin's source
+        const int start = a.poff[hid], end = start + LD(a.cdeg[hid]);
+        const int nx = a.apos[tw] + 1;
+        int succ;
+        if (nx == end) {
+            const bool is_root = LD(a.minp[LD(a.eroot[j >> 1])]) == LD(a.ep[tw]);
+            succ = is_root ? NIL : start;
+        } else {
+            succ = nx;
+        }
+        const int si = a.apos[j];
+        snc[si] = succ;
+        svc[si] = 1;
+    }
+    __syncthreads();
+    int *rank = nullptr;
+    const int rounds = rank_block(ctl, svc, svn, snc, snn, ncore, &rank);
+    for (long long t = threadIdx.x; t < nce; t += blockDim.x) {
+        const long long i = LD(a.cel[t]);
+        orient_one(a, i, rank[a.apos[2 * i]] > rank[a.apos[2 * i + 1]], ep);
+    }
+    if (threadIdx.x == 0) {
+        ctl->ncore = (u64)ncore;
+        ctl->rank_rounds = rounds;
+    }
+}
+
 // Orientation of E_r (Algorithm 2, phase 2).  The replacement edges form a
 // forest over the pieces (the super-forest); each super-tree is rooted at
 // its piece with the smallest root id.  A non-root piece with a single
@@ -959,7 +1116,13 @@ __global__ void __launch_bounds__(ORIENT_THREADS) k_orient(Ctl *ctl, OrientArgs 
     // (ep), later phases its dense id (eid) and each edge's super-tree root
     // (eroot), so no phase re-walks rep / pidx / the hook forest.
     // phase 1: dense ids for the pieces touched by E_r
-    if (gtid() == 0) ctl->ncore = 0;
+    if (gtid() == 0) ctl->ncore = ctl->cnt[0] = 0;
+    // the path walks after this kernel follow parent pointers one dependent
+    // load at a time: pull the forest into L2 now, while the phases below
+    // wait at their barriers (one 128-byte line per thread or so)
+    if (ner > 0)
+        for (long long l = gtid(); l < (a.n + 31) / 32; l += gstride())
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.parent + 32 * l));
     // (block-uniform loop: the dense ids are reserved once per block)
     for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < 2 * ner; b0 += gstride()) {
         const long long j = b0 + threadIdx.x;
@@ -982,6 +1145,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS) k_orient(Ctl *ctl, OrientArgs 
             a.pdeg[id] = 0;
             a.cdeg[id] = 0;
             a.pcur[id] = 0;
+            a.poff[id] = -1;   // (claimed by the core path for small cores)
             // the root piece of the hook forest holds its super-tree's slot
             if (find_root(a.comp, p, ctl) == p) a.minp[p] = INT_MAX;
         }
@@ -1021,8 +1185,31 @@ __global__ void __launch_bounds__(ORIENT_THREADS) k_orient(Ctl *ctl, OrientArgs 
             unsigned g1 = __match_any_sync(core, id1);
             if ((int)(threadIdx.x & 31) == __ffs(g1) - 1) atomicAdd(&a.cdeg[id1], __popc(g1));
         }
+        // the core edges, listed for the one-block path of small cores
+        if (!lf) {
+            const int ld = __ffs(core) - 1;
+            u64 b = 0;
+            if ((int)(threadIdx.x & 31) == ld) b = atomicAdd(&ctl->cnt[0], (u64)__popc(core));
+            b = __shfl_sync(core, b, ld);
+            a.cel[b + __popc(core & ((1u << (threadIdx.x & 31)) - 1u))] = (int)i;
+        }
     }
     if (!grid_barrier(ctl, bar)) return;
+    {
+        // A small core (most batches: the leaves are most of E_r) is done by
+        // block 0 alone with block barriers (adjacency, Euler successors,
+        // ranking in shared memory, orientation), while every block orients
+        // the leaf edges; a large one takes the grid phases below.
+        const long long nce = (long long)*(volatile u64 *)&ctl->cnt[0];
+        if (nce <= ORIENT_SMALL_EDGES) {
+            for (long long i = gtid(); i < ner; i += gstride()) {
+                const unsigned char lf = LD(a.lf[i]);
+                if (lf) orient_one(a, i, lf == 2, ep);
+            }
+            if (blockIdx.x == 0) orient_small_core(ctl, a, nce, ep);
+            return;
+        }
+    }
     // phase 3: adjacency ranges of the core pieces, reserved per block from
     // one cursor (ctl->ncore ends as the number of core arcs; the order of
     // the ranges is immaterial)
@@ -1088,26 +1275,10 @@ __global__ void __launch_bounds__(ORIENT_THREADS) k_orient(Ctl *ctl, OrientArgs 
                 snc[i] = LD(a.nx0[i]);
             }
             __syncthreads();
-            for (;; ++r) {
-                int ch = 0;
-                for (long long i = threadIdx.x; i < ncore; i += blockDim.x) {
-                    int sx = snc[i];
-                    if (sx != NIL) {
-                        svn[i] = svc[i] + svc[sx];
-                        snn[i] = snc[sx];
-                        ch = 1;
-                    } else {
-                        svn[i] = svc[i];
-                        snn[i] = NIL;
-                    }
-                }
-                int any = __syncthreads_or(ch);
-                int *t = svc; svc = svn; svn = t;
-                t = snc; snc = snn; snn = t;
-                if (!any || r >= MAX_ROUNDS) break;
-            }
-            for (long long i = threadIdx.x; i < ncore; i += blockDim.x) a.val0[i] = svc[i];
-            if (threadIdx.x == 0) ctl->rank_rounds = r + 1;
+            int *rank = nullptr;
+            const int rounds = rank_block(ctl, svc, svn, snc, snn, (int)ncore, &rank);
+            for (long long i = threadIdx.x; i < ncore; i += blockDim.x) a.val0[i] = rank[i];
+            if (threadIdx.x == 0) ctl->rank_rounds = rounds;
         }
         if (!grid_barrier(ctl, bar)) return;
         vc = a.val0;
@@ -1141,23 +1312,9 @@ __global__ void __launch_bounds__(ORIENT_THREADS) k_orient(Ctl *ctl, OrientArgs 
     }
     // phase 7: orient, attach points, new roots
     for (long long i = gtid(); i < ner; i += gstride()) {
-        u64 k = a.er[i];
-        int x0 = (int)klo(k), x1 = (int)khi(k);
-        int p0 = LD(a.ep[2 * i]), p1 = LD(a.ep[2 * i + 1]);
-        unsigned char lf = LD(a.lf[i]);
-        bool down;                                 // true: p0 is the parent of p1
-        if (lf) down = lf == 2;
-        else down = LD(vc[LD(a.apos[2 * i])]) > LD(vc[LD(a.apos[2 * i + 1])]);
-        int child = down ? p1 : p0;
-        int x = down ? x1 : x0, y = down ? x0 : x1;
-        a.chx[i] = x;
-        a.chy[i] = y;
-        // each non-root piece is the child of exactly one edge: one write
-        // per piece; the super-root keeps its representative
-        a.att_x[child] = x;
-        a.att_ep[child] = ep;
-        a.newrep[child] = LD(a.minp[LD(a.eroot[i])]);
-        a.rep_ep[child] = ep;
+        const unsigned char lf = LD(a.lf[i]);
+        const bool down = lf ? lf == 2 : LD(vc[LD(a.apos[2 * i])]) > LD(vc[LD(a.apos[2 * i + 1])]);
+        orient_one(a, i, down, ep);
     }
 }
 
@@ -1209,58 +1366,67 @@ __global__ void k_walk(Ctl *ctl, const int *chx, const int *chy, const int *rep,
 // piece that is re-rooted at an attach point x != its root is active (its
 // old parent is saved, J0 seeded, x marked); every vertex of a merged piece
 // takes the super-tree's root as its new rep.
-__global__ void k_active(const int *L, int use_list, long long cnt_static, Ctl *ctl, int *rep, const int *parent,
-                         const unsigned *sel_ep, const int *att_x, const unsigned *rep_ep, const int *newrep,
-                         int *act, int *pold, int *J0, unsigned char *mark, int *aidx, int *aroot) {
+// IP items per thread and iteration (IPT over a list, IPN over all
+// vertices), k-major as in k_aff_collect, one slot reservation per block.
+// Only the pieces stay in registers; the few items whose piece changed are
+// handled from bit masks (the common item costs one stamp gather).
+template <int IP>
+__global__ void __launch_bounds__(BLK)
+    k_active(const int *L, int use_list, long long cnt_static, Ctl *ctl, int *rep, const int *parent,
+             const unsigned *sel_ep, const int *att_x, const unsigned *rep_ep, const int *newrep, int *act, int *pold,
+             int *J0, unsigned char *mark, int *aidx, int *aroot) {
+    static_assert(IP <= 32, "item masks are 32 bits");
     if (*(volatile int *)&ctl->skip) return;
     unsigned ep = ctl->epoch;
     long long cnt = use_list ? (long long)ctl->naff : cnt_static;
-    // IPT consecutive items per thread and iteration, one slot reservation
-    // per block (as in k_aff_collect)
-    const long long step = (long long)gridDim.x * blockDim.x * IPT;
-    for (long long b0 = (long long)blockIdx.x * blockDim.x * IPT; b0 < cnt; b0 += step) {
-        const long long i0 = b0 + (long long)threadIdx.x * IPT;
-        int v[IPT], p[IPT], x[IPT];
-        bool on[IPT], chg[IPT];
+    const long long step = (long long)gridDim.x * blockDim.x * IP;
+    for (long long b0 = (long long)blockIdx.x * blockDim.x * IP; b0 < cnt; b0 += step) {
+        const long long i0 = b0 + threadIdx.x;
+        int p[IP];
         if (use_list) {
-            load_ipt(L, i0, cnt, v);
 #pragma unroll
-            for (int k = 0; k < IPT; ++k) p[k] = i0 + k < cnt ? rep[v[k]] : 0;
+            for (int k = 0; k < IP; ++k) {
+                const long long i = i0 + (long long)k * blockDim.x;
+                p[k] = i < cnt ? L[i] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < IP; ++k) p[k] = i0 + (long long)k * blockDim.x < cnt ? rep[p[k]] : 0;
         } else {
 #pragma unroll
-            for (int k = 0; k < IPT; ++k) v[k] = (int)(i0 + k);
-            load_ipt(rep, i0, cnt, p);
+            for (int k = 0; k < IP; ++k) {
+                const long long i = i0 + (long long)k * blockDim.x;
+                p[k] = i < cnt ? rep[i] : 0;
+            }
         }
         // the pieces selected for the marks are re-rooted child pieces, all
         // of which get a new representative: one gather in the common case
+        unsigned chg = 0;
 #pragma unroll
-        for (int k = 0; k < IPT; ++k) chg[k] = i0 + k < cnt && rep_ep[p[k]] == ep;
-        int c = 0;
-#pragma unroll
-        for (int k = 0; k < IPT; ++k) {
-            on[k] = false;
-            x[k] = -1;
-            if (chg[k] && sel_ep[p[k]] == ep) {
-                x[k] = att_x[p[k]];
-                on[k] = x[k] != p[k];
-            }
-            c += on[k];
+        for (int k = 0; k < IP; ++k)
+            if (i0 + (long long)k * blockDim.x < cnt && rep_ep[p[k]] == ep) chg |= 1u << k;
+        unsigned on = 0;
+        for (unsigned m = chg; m; m &= m - 1) {
+            const int k = __ffs(m) - 1;
+            const int pk = p[k];
+            if (sel_ep[pk] == ep && att_x[pk] != pk) on |= 1u << k;
         }
-        long long q = block_reserve(&ctl->nact, c);
-#pragma unroll
-        for (int k = 0; k < IPT; ++k) {
-            if (i0 + k >= cnt) continue;
-            if (on[k]) {
-                int pv = parent[v[k]];
-                act[q] = v[k];
+        long long q = block_reserve(&ctl->nact, __popc(on));
+        for (unsigned m = chg; m; m &= m - 1) {
+            const int k = __ffs(m) - 1;
+            const int pk = p[k];
+            const long long i = i0 + (long long)k * blockDim.x;
+            const int v = use_list ? L[i] : (int)i;
+            if ((on >> k) & 1u) {
+                const int pv = parent[v];
+                act[q] = v;
                 pold[q] = pv;
-                J0[v[k]] = pv;
-                mark[v[k]] = v[k] == x[k];
-                aidx[v[k]] = (int)q;   // dense index (Euler-tour marks)
-                aroot[q] = p[k];       // the piece root
+                J0[v] = pv;
+                mark[v] = v == att_x[pk];
+                aidx[v] = (int)q;   // dense index (Euler-tour marks)
+                aroot[q] = pk;      // the piece root
                 ++q;
             }
-            if (chg[k]) rep[v[k]] = newrep[p[k]];
+            rep[v] = newrep[pk];
         }
     }
 }
@@ -1380,8 +1546,10 @@ static unsigned coop_blocks(const void *fn, int nsm, int cap_per_sm) {
 // The vertex passes (k_aff_collect, k_active) loop over their range with
 // the blocks that are resident at once: no partial last wave.
 unsigned grid_vertex_pass(int nsm) {
-    unsigned a = coop_blocks((const void *)k_aff_collect, nsm, 8), b = coop_blocks((const void *)k_active, nsm, 8);
-    return a < b ? a : b;
+    unsigned a = coop_blocks((const void *)k_aff_collect, nsm, 8),
+             b = coop_blocks((const void *)k_active<IPN>, nsm, 8),
+             c = coop_blocks((const void *)k_active<IPT>, nsm, 8);
+    return a < b ? (a < c ? a : c) : (b < c ? b : c);
 }
 unsigned coop_blocks_jump(int nsm) {
     // the three root-search variants share one launch bound; take the least
@@ -1466,8 +1634,12 @@ cudaError_t launch_active(const Dev &d, const int *L, int use_list, long long cn
                           const int *parent, const unsigned *sel_ep, const int *att_x, const unsigned *rep_ep,
                           const int *newrep, int *act, int *pold, int *J0, unsigned char *mark, int *aidx,
                           int *aroot, cudaStream_t s) {
-    k_active<<<d.grid_pass, BLK, 0, s>>>(L, use_list, cnt_static, ctl, rep, parent, sel_ep, att_x, rep_ep, newrep, act,
-                                pold, J0, mark, aidx, aroot);
+    if (use_list)
+        k_active<IPT><<<d.grid_pass, BLK, 0, s>>>(L, use_list, cnt_static, ctl, rep, parent, sel_ep, att_x, rep_ep,
+                                                  newrep, act, pold, J0, mark, aidx, aroot);
+    else
+        k_active<IPN><<<d.grid_pass, BLK, 0, s>>>(L, use_list, cnt_static, ctl, rep, parent, sel_ep, att_x, rep_ep,
+                                                  newrep, act, pold, J0, mark, aidx, aroot);
     return cudaGetLastError();
 }
 cudaError_t launch_mark(const Dev &d, Ctl *ctl, const int *act, int *J0, int *J1, unsigned char *mark,

@@ -106,6 +106,9 @@ struct OrientArgs {
     int *cdeg;           // core degree per dense piece
     int *ep, *eid;       // per arc: source piece, its dense id
     int *eroot;          // per edge: hook-forest root of its super-tree
+    int *cel;            // core edges (for the one-block path of small cores)
+    const int *parent;   // the forest: pulled into L2 for the walks that follow
+    long long n;
 };
 cudaError_t launch_orient(const Dev &d, Ctl *ctl, OrientArgs a, cudaStream_t s);
 cudaError_t launch_walk(const Dev &d, Ctl *ctl, const int *chx, const int *chy, const int *rep, int *parent,
