@@ -206,8 +206,12 @@ def phase_bytes(st: dict, n: int, op: int) -> dict:
     b, a = st["batch_len"], st["applied"]
     out = {"begin": 8 * b}
     if op == 0:
-        out["ins_claim"] = 16 * b + 64 * a
-        out["ins_place"] = 16 * a + 8 * st["candidates"]
+        # one kernel: batch read, index claim (two 32-byte probes), CSR
+        # append, candidate writes; the supergraph variant then compacts
+        # the pair table
+        out["ins_claim"] = 16 * b + 80 * a + 8 * st["candidates"]
+        if st.get("supergraph"):
+            out["ins_place"] = 16 * st["candidates"]
         out["active"] = 8 * n
     else:
         aff = st["affected"]

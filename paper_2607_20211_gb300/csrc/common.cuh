@@ -133,6 +133,27 @@ __device__ __forceinline__ long long index_claim(Index ix, u64 key) {
     return LLONG_MIN;
 }
 
+// Hook-forest slots of the candidates' endpoints (read by k_boruvka): the
+// kernel that writes a candidate sets up each of its endpoints once per
+// batch (whoever stamps it first): its own root in comp, both per-round
+// minimum slots empty.
+struct HookSlots {
+    unsigned *stamp;
+    int *comp;
+    u64 *best0, *best1;
+};
+__device__ __forceinline__ void hook_slot_init(const HookSlots &hs, int a, unsigned ep) {
+    // one lane per endpoint among the calling lanes (the giant tree's root
+    // is an endpoint of most candidates)
+    const unsigned grp = __match_any_sync(__activemask(), a);
+    if ((int)(threadIdx.x & 31) != __ffs(grp) - 1) return;
+    if (__ldcg(&hs.stamp[a]) != ep && atomicExch(&hs.stamp[a], ep) != ep) {
+        hs.comp[a] = a;
+        hs.best0[a] = EMPTY_KEY;
+        hs.best1[a] = EMPTY_KEY;
+    }
+}
+
 // Lookup; -1 when absent.  Deleted entries (TOMB_KEY) are probed past.
 __device__ __forceinline__ long long index_find(Index ix, u64 key) {
     u64 s = hslot(key, ix.mask);

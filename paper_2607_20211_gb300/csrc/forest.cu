@@ -26,7 +26,9 @@
 // edges, slower for the 100K batches' cores of about 900 edges)
 #define ORIENT_SMALL_EDGES 256
 // independent items per thread and iteration in the pointer-doubling rounds
+#ifndef JU
 #define JU 4
+#endif
 // the same for the final pass of the jump (more state per item)
 #define JF 2
 // consecutive items per thread in the list-building vertex passes: IPT over
@@ -220,6 +222,58 @@ __device__ __forceinline__ void warp_fill_tiles(int *tile, bool on, long long st
     }
 }
 
+// Append the non-empty rows (`f`, `len` > 0) of a warp's lanes to the row
+// list of the scan, with their entry ranges and the tile map: positions are
+// pb (rows << 32 | entries) plus offsets from one atomic per warp on the
+// packed counter pc.  All 32 lanes call.
+__device__ __forceinline__ void warp_list_rows(u64 *pc, u64 pb, RowList rl, Csr g, bool f, int w, int len, int p,
+                                               int ro) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned fm = __ballot_sync(0xffffffffu, f);
+    if (!fm) return;
+    // exclusive warp scan of the row lengths
+    int x = f ? len : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const int tot = __shfl_sync(0xffffffffu, x, 31);
+    const int ex = x - (f ? len : 0);
+    const int fl = __ffs(fm) - 1;
+    u64 base = 0;
+    if (lane == fl) base = atomicAdd(pc, ((u64)__popc(fm) << 32) | (u64)(unsigned)tot);
+    base = __shfl_sync(0xffffffffu, base, fl) + pb;
+    const long long q = (long long)(base >> 32) + __popc(fm & lt);
+    const long long eo = (long long)(base & 0xFFFFFFFFull) + ex;
+    if (f) {
+        rl.D[q] = w;
+        rl.roff[q] = (unsigned)eo;
+        rl.base[q] = (unsigned)g.off[w];
+        rl.meta[q] = make_int2(p, ro);
+    }
+    warp_fill_tiles(rl.tile, f, eo, len, (int)q);
+}
+
+// Append one warp's detached vertices (lanes with `on`) to the vertex list
+// and their non-empty rows (`len` > 0) to the row list of the scan: positions
+// are the level's bases (vb vertices; pb rows << 32 | entries) plus offsets
+// taken from the level's own counters (vc, and pc packed like pb), one
+// atomic per warp on each.  All 32 lanes call.
+__device__ __forceinline__ void warp_detach_append(u64 *vc, u64 *pc, long long vb, u64 pb, RowList rl, int *A, Csr g,
+                                                   bool on, int w, int len, int p, int ro) {
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(0xffffffffu, on);
+    if (!m) return;
+    const int ld = __ffs(m) - 1;
+    u64 a0 = 0;
+    if (lane == ld) a0 = atomicAdd(vc, (u64)__popc(m));
+    a0 = __shfl_sync(0xffffffffu, a0, ld);
+    if (on) A[vb + (long long)a0 + __popc(m & ((1u << lane) - 1u))] = w;
+    warp_list_rows(pc, pb, rl, g, on && len > 0, w, len, p, ro);
+}
+
 // Representatives by asynchronous pointer doubling in place (delete batches
 // with DRSF_JUMP=async): no grid barrier between steps.  J holds a copy of
 // the cut forest for the listed vertices; afterwards J[v] is the complemented
@@ -300,48 +354,6 @@ __global__ void __launch_bounds__(BLK, 6) k_jump_async(const int *A, Ctl *ctl, i
 // non-empty row (`len` > 0) consecutive rows of the row list and their entry
 // ranges, from one atomic per warp on each counter (rows in the high and
 // entries in the low 32 bits of the packed row counter).  All 32 lanes call.
-// Append one warp's detached vertices (lanes with `on`) to the vertex list
-// and their non-empty rows to the row list of the scan: positions are the
-// level's bases (vb vertices; pb rows << 32 | entries) plus offsets taken
-// from the level's own counters (vc, pc), one atomic per warp on each.
-__device__ __forceinline__ void warp_detach_append(u64 *vc, u64 *pc, long long vb, u64 pb, RowList rl, int *A, Csr g,
-                                                   bool on, int w, int len, int p, int ro) {
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    const unsigned m = __ballot_sync(0xffffffffu, on);
-    if (!m) return;
-    const int ld = __ffs(m) - 1;
-    u64 a0 = 0;
-    if (lane == ld) a0 = atomicAdd(vc, (u64)__popc(m));
-    a0 = __shfl_sync(0xffffffffu, a0, ld);
-    if (on) A[vb + (long long)a0 + __popc(m & lt)] = w;
-    const bool f = on && len > 0;
-    const unsigned fm = __ballot_sync(0xffffffffu, f);
-    if (!fm) return;
-    // exclusive warp scan of the row lengths
-    int x = f ? len : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    const int tot = __shfl_sync(0xffffffffu, x, 31);
-    const int ex = x - (f ? len : 0);
-    const int fl = __ffs(fm) - 1;
-    u64 base = 0;
-    if (lane == fl) base = atomicAdd(pc, ((u64)__popc(fm) << 32) | (u64)(unsigned)tot);
-    base = __shfl_sync(0xffffffffu, base, fl) + pb;
-    const long long q = (long long)(base >> 32) + __popc(fm & lt);
-    const long long eo = (long long)(base & 0xFFFFFFFFull) + ex;
-    if (f) {
-        rl.D[q] = w;
-        rl.roff[q] = (unsigned)eo;
-        rl.base[q] = (unsigned)g.off[w];
-        rl.meta[q] = make_int2(p, ro);
-    }
-    warp_fill_tiles(rl.tile, f, eo, len, (int)q);
-}
-
 // Delete, top-down alternative to the pointer jumping of Algorithm 1 (same
 // representatives): the detached vertices are the cut vertices and every
 // descendant of one in the cut forest, and a detached vertex's piece is the
@@ -885,32 +897,19 @@ __device__ __forceinline__ void hm_flush(HotMin &t, u64 *arr, u64 *rst_arr) {
 // distinct keys this is Boruvka's algorithm: E_r is the unique minimum
 // spanning forest of the piece multigraph, |E_r| = k - l.
 __global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1, int *comp,
-                          u64 *best0, u64 *best1, u64 *er, long long er_cap, unsigned *hstamp) {
+                          u64 *best0, u64 *best1, u64 *er, long long er_cap) {
     if (*(volatile int *)&ctl->skip) return;
     __shared__ HotMin hm;
-    const unsigned ep = ctl->epoch;
-    long long c0 = (long long)ctl->ncand;
-    // initialise each candidate endpoint once (the first lane to stamp it)
-    for (long long i = gtid(); i < c0; i += gstride()) {
-        int e2[2] = {ca0[i], cb0[i]};
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const int a = e2[s];
-            unsigned grp = __match_any_sync(__activemask(), a);
-            if ((int)(threadIdx.x & 31) == __ffs(grp) - 1 && __ldcg(&hstamp[a]) != ep &&
-                atomicExch(&hstamp[a], ep) != ep) {
-                comp[a] = a;
-                best0[a] = best1[a] = EMPTY_KEY;
-            }
-        }
-    }
+    // every candidate endpoint's comp / best slots were set up by the kernel
+    // that wrote the candidate (hook_slot_init), so round 0 starts at once;
+    // the round-0 list is the candidate list itself
+    const long long c0 = (long long)ctl->ncand;
     if (gtid() == 0) {
-        ctl->cnt[0] = (u64)c0;
         ctl->cnt[1] = ctl->cnt[2] = 0;
         ctl->flag[0] = ctl->flag[1] = ctl->flag[2] = 0;
     }
     hm_init(hm);
-    if (!grid_barrier(ctl, &ctl->bar[1])) return;
+    __syncthreads();
     int r = 0;
     for (;; ++r) {
         if (r >= MAX_ROUNDS) {
@@ -921,7 +920,7 @@ __global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int 
         int *ca = (r & 1) ? ca1 : ca0, *can = (r & 1) ? ca0 : ca1;
         int *cb = (r & 1) ? cb1 : cb0, *cbn = (r & 1) ? cb0 : cb1;
         u64 *best = (r & 1) ? best1 : best0, *bestn = (r & 1) ? best0 : best1;
-        long long c = (long long)*(volatile u64 *)&ctl->cnt[r % 3];
+        long long c = r == 0 ? c0 : (long long)*(volatile u64 *)&ctl->cnt[r % 3];
         if (gtid() == 0) {
             ctl->cnt[(r + 2) % 3] = 0;
             ctl->flag[(r + 1) % 3] = 0;
@@ -1613,11 +1612,9 @@ cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_
     return cudaLaunchCooperativeKernel(fn, d.coop_jump, BLK, args, 0, s);
 }
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
-                           int *comp, u64 *best0, u64 *best1, u64 *er, long long er_cap, unsigned *hstamp,
-                           cudaStream_t s) {
+                           int *comp, u64 *best0, u64 *best1, u64 *er, long long er_cap, cudaStream_t s) {
     void *args[] = {(void *)&ctl, (void *)&ck0, (void *)&ca0, (void *)&cb0, (void *)&ck1, (void *)&ca1,
-                    (void *)&cb1, (void *)&comp, (void *)&best0, (void *)&best1, (void *)&er, (void *)&er_cap,
-                    (void *)&hstamp};
+                    (void *)&cb1, (void *)&comp, (void *)&best0, (void *)&best1, (void *)&er, (void *)&er_cap};
     return cudaLaunchCooperativeKernel((const void *)k_boruvka, d.coop_hook, BLK, args, 0, s);
 }
 cudaError_t launch_orient(const Dev &d, Ctl *ctl, OrientArgs a, cudaStream_t s) {
