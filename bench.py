@@ -206,12 +206,8 @@ def phase_bytes(st: dict, n: int, op: int) -> dict:
     b, a = st["batch_len"], st["applied"]
     out = {"begin": 8 * b}
     if op == 0:
-        # one kernel: batch read, index claim (two 32-byte probes), CSR
-        # append, candidate writes; the supergraph variant then compacts
-        # the pair table
-        out["ins_claim"] = 16 * b + 80 * a + 8 * st["candidates"]
-        if st.get("supergraph"):
-            out["ins_place"] = 16 * st["candidates"]
+        out["ins_claim"] = 16 * b + 64 * a
+        out["ins_place"] = 16 * a + 8 * st["candidates"]
         out["active"] = 8 * n
     else:
         aff = st["affected"]
@@ -554,7 +550,12 @@ def run_batched(args, rank, ws, local):
                 tot += e0.elapsed_time(e1)
         return tot / 1e3
 
+    # every form sizes its per-batch buffers for the largest batch first, so
+    # no timed step grows them (a growth synchronises, reallocates and drops
+    # the captured launch sequences)
+    umax = max(int(b.shape[0]) for pair in ubat for b in pair)
     f = drsf.DynamicForest(U.n, edges_u, par_u)
+    f.reserve(umax)
     barrier()
     t_union = timed(lambda k: (f.apply(0, ubat[k][0]), f.apply(1, ubat[k][1])))
     final = f.parent().cpu().numpy()
@@ -582,6 +583,7 @@ def run_batched(args, rank, ws, local):
                               log=lambda m: print(m, file=sys.stderr))
         del e1, p1
     f = drsf.DynamicForest(U.n, edges_u, par_u)
+    f.reserve(umax)
     t_persist = timed(lambda k: (f.apply_batched(0, ubat[k][0], voff, boffs[k][0], sched[0]),
                                  f.apply_batched(1, ubat[k][1], voff, boffs[k][1], sched[1])))
     final_p = f.parent().cpu().numpy()
@@ -589,6 +591,8 @@ def run_batched(args, rank, ws, local):
     if not np.array_equal(final_p, final_plan):
         raise RuntimeError("persistent per-graph kernels diverged from the grid-wide path")
     hs = [drsf.DynamicForest(g.n, dev(g.edges()), dev(g.parent)) for g in graphs]
+    for i, h in enumerate(hs):
+        h.reserve(max(int(gbat[k][op][i].shape[0]) for k in range(W + K) for op in (0, 1)))
 
     def per_graph(k):
         for op in (0, 1):

@@ -129,8 +129,8 @@ struct drsf_ctx {
 // Phases of one batch, in launch order.
 enum {
     PH_BEGIN = 0,     // k_begin + id validation
-    PH_INS_CLAIM,     // insert: normalisation, index claim, CSR append, cross test (one kernel)
-    PH_INS_PLACE,     // insert, supergraph variant: pair-table compaction
+    PH_INS_CLAIM,     // insert: normalisation + index claim
+    PH_INS_PLACE,     // insert: CSR append + cross test
     PH_DEL_CLAIM,     // delete: normalisation, removal, tree-edge cut
     PH_AFF,           // delete: affected-vertex list
     PH_JUMP,          // delete: pointer jumping (representatives)
@@ -679,20 +679,18 @@ static bool use_supergraph(const drsf_ctx *h, int op, long long len) {
 static drsf_status launch_rest(drsf_ctx *h, int op, bool sg, long long glen, cudaStream_t s) {
     Ctl *ctl = h->ctl;
     Csr g{h->off, h->used, h->col};
-    CK(launch_validate_batch(glen, h->n, ctl, s));
+    CK(launch_validate_batch(glen, h->n, ctl, h->rep, h->parent, h->off, s));
     prof_end(h, PH_BEGIN, 2, s);
     if (op == DRSF_INSERT) {
         // Algorithm 1, insert: F^ = F, M = B; rep of the previous batch is current
         prof_begin(h, PH_INS_CLAIM, s);
-        CK(launch_ins(glen, ctl, g, h->ix, h->ovf, h->ovf_cap, h->rep, sg, h->pt, h->ck[0], h->ca[0], h->cb[0],
-                      h->cand_cap, hook_slots(h), s));
+        CK(launch_ins_claim(glen, h->ix, ctl, h->nkey, h->nslot, s));
         prof_end(h, PH_INS_CLAIM, 1, s);
-        if (sg) {
-            prof_begin(h, PH_INS_PLACE, s);
-            CK(launch_pairs_compact(h->dev, ctl, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, hook_slots(h),
-                                    s));
-            prof_end(h, PH_INS_PLACE, 1, s);
-        }
+        prof_begin(h, PH_INS_PLACE, s);
+        CK(launch_ins_place(h->dev, h->nkey, h->nslot, ctl, g, h->ix, h->ovf, h->ovf_cap, h->rep, sg, h->pt,
+                            h->ck[0], h->ca[0], h->cb[0], h->cand_cap, hook_slots(h), s));
+        if (sg) CK(launch_pairs_compact(h->dev, ctl, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
+        prof_end(h, PH_INS_PLACE, sg ? 2 : 1, s);
     } else {
         // Algorithm 1, delete: remove B, cut tree edges, re-label the cut trees
         prof_begin(h, PH_DEL_CLAIM, s);
@@ -706,7 +704,7 @@ static drsf_status launch_rest(drsf_ctx *h, int op, bool sg, long long glen, cud
             const long long n = h->n;
             CK(launch_detach(h->dev, ctl, h->cutlist, h->parent, h->rep, g, h->ovf, h->ovf_cap, rows(h), h->A, h->J1,
                              h->det_ep, h->det_claim, h->rold, std::max<long long>(1 << 16, n / 8),
-                             std::max<long long>(1 << 20, 4 * n), 256, h->act, h->xlist, s));
+                             std::max<long long>(1 << 20, 4 * n), DETACH_LEVELS, h->act, h->xlist, s));
             prof_end(h, PH_JUMP, 1, s);
         }
         prof_begin(h, PH_AFF, s);
@@ -720,17 +718,17 @@ static drsf_status launch_rest(drsf_ctx *h, int op, bool sg, long long glen, cud
         prof_end(h, PH_JUMP, h->jump_sync == 2 ? 2 : 1, s);   // the asynchronous doubling is a launch of its own
         prof_begin(h, PH_SCAN, s);
         CK(launch_scan_rows(h->dev, rows(h), ctl, g, h->rep, sg, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap,
-                            hook_slots(h), s));
-        CK(launch_scan_ovf(h->dev, h->ovf, ctl, h->rep, sg, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap,
-                           hook_slots(h), s));
-        if (sg)
-            CK(launch_pairs_compact(h->dev, ctl, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, hook_slots(h),
-                                    s));
+                            s));
+        CK(launch_scan_ovf(h->dev, h->ovf, ctl, h->rep, sg, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
+        if (sg) CK(launch_pairs_compact(h->dev, ctl, h->pt, h->ck[0], h->ca[0], h->cb[0], h->cand_cap, s));
         prof_end(h, PH_SCAN, sg ? 3 : 2, s);
     }
     prof_begin(h, PH_HOOK, s);
-    CK(launch_boruvka(h->dev, ctl, h->ck[0], h->ca[0], h->cb[0], h->ck[1], h->ca[1], h->cb[1], h->comp, h->best0,
-                      h->best1, h->er, h->n, s));
+    // an HS insert's candidates all come from k_ins_place, which set up
+    // their hook-forest slots; otherwise the hooking sets them up itself
+    // (inside the scan of a large delete that costs more than it saves)
+    CK(launch_boruvka(h->dev, ctl, h->ck[0], h->ca[0], h->cb[0], h->ck[1], h->ca[1], h->cb[1], hook_slots(h), h->er,
+                      h->n, (op == DRSF_INSERT && !sg) ? 0 : 1, s));
     prof_end(h, PH_HOOK, 1, s);
     OrientArgs oa{};
     oa.er = h->er;

@@ -52,6 +52,9 @@ struct Ctl {
     u64 dv[3], dp[3];       // top-down delete, per level (ring of 3): vertices appended, and
                             // rows << 32 | entries appended
     u64 dovf;               // top-down delete: tree edges listed from the overflow list
+    unsigned depth_hint;    // top-down delete, kept across batches: levels the last search took, or
+                            // above the level limit after one gave up (counts down once per skip)
+    int det_skip;           // the batch skipped the top-down search (read by the next k_begin)
     u64 nb;                 // normalised batch edges (new / deleted keys)
     u64 ncut;               // cut vertices
     u64 naff;               // affected list
@@ -131,6 +134,16 @@ __device__ __forceinline__ long long index_claim(Index ix, u64 key) {
         s = (s + 1) & ix.mask;
     }
     return LLONG_MIN;
+}
+
+// Pull a whole array into L2, one prefetch per 128-byte line, strided over
+// the calling threads (thread tid of nthreads): for arrays that the next
+// kernels gather from at random, which would otherwise pay one DRAM latency
+// per dependent access.
+__device__ __forceinline__ void l2_prefetch(const void *p, long long bytes, long long tid, long long nthreads) {
+    const char *c = (const char *)p;
+    for (long long off = tid * 128; off < bytes; off += nthreads * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(c + off));
 }
 
 // Hook-forest slots of the candidates' endpoints (read by k_boruvka): the

@@ -36,6 +36,9 @@
 // passes are one dependent gather behind a streaming load)
 #define IPT 4
 #define IPN 16
+// top-down delete: after a search that gave up at its level limit, the
+// deletes that skip it before it is tried again
+#define DETACH_BACKOFF 8
 // longest path reversed by one walking thread (longer ones: doubling marks)
 #define WALK_MAX 64
 
@@ -90,6 +93,10 @@ __global__ void k_begin(Ctl *ctl, int op, long long len, const int *batch) {
     ctl->hook_rounds = ctl->rank_rounds = ctl->mark_rounds = ctl->jump_rounds = ctl->reversed = 0;
     ctl->jump_visits = 0;
     ctl->td = ctl->need_root = 0;
+    if (ctl->det_skip) {   // the last batch skipped the top-down search
+        if (ctl->depth_hint > 0) ctl->depth_hint -= 1;
+        ctl->det_skip = 0;
+    }
     ctl->det_levels = ctl->det_entries = 0;
     ctl->batch_len = len;
     for (int i = 0; i < 3; ++i) {
@@ -378,6 +385,17 @@ __global__ void __launch_bounds__(BLK, 4)
              int *A, int *J1, unsigned *det_ep, unsigned *det_claim, const int *rold, long long budget_v,
              long long budget_e, int max_levels, int *oc, int *op) {
     if (*(volatile int *)&ctl->skip) return;
+    // Deep trees below the cuts make the search a long chain of levels
+    // (one grid barrier each) where pointer doubling needs a logarithmic
+    // number of steps: after a search that gave up at the level limit the
+    // next DETACH_BACKOFF deletes go straight to pointer jumping, then the
+    // search is tried again.  The hint is not written in this launch before
+    // every block has read it (the next batch's k_begin counts it down), so
+    // all blocks take the same branch.
+    if (*(volatile unsigned *)&ctl->depth_hint > (unsigned)max_levels) {
+        if (gtid() == 0) ctl->det_skip = 1;
+        return;
+    }
     const unsigned ep = ctl->epoch;
     const long long nc = (long long)ctl->ncut;
     u64 *bar = &ctl->bar[6];
@@ -523,7 +541,10 @@ __global__ void __launch_bounds__(BLK, 4)
     // over budget: nothing was published (naff, ndet and rep untouched);
     // the pointer-jumping path takes over from the cut
     if (!ok) {
-        if (gtid() == 0) ctl->det_levels = -lvl;
+        if (gtid() == 0) {
+            ctl->det_levels = -lvl;
+            if (lvl >= max_levels) ctl->depth_hint = (unsigned)max_levels + DETACH_BACKOFF;
+        }
         return;
     }
     // commit the representatives of the detached vertices
@@ -537,6 +558,7 @@ __global__ void __launch_bounds__(BLK, 4)
         ctl->det_entries = (long long)(pb & 0xFFFFFFFFull);
         rl.roff[pb >> 32] = (unsigned)pb;
         ctl->det_levels = lvl;
+        ctl->depth_hint = (unsigned)lvl;
         ctl->td = 1;
     }
 }
@@ -896,20 +918,31 @@ __device__ __forceinline__ void hm_flush(HotMin &t, u64 *arr, u64 *rst_arr) {
 // component are dropped, the rest are compacted for the next round.  With
 // distinct keys this is Boruvka's algorithm: E_r is the unique minimum
 // spanning forest of the piece multigraph, |E_r| = k - l.
-__global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1, int *comp,
-                          u64 *best0, u64 *best1, u64 *er, long long er_cap) {
+__global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1, HookSlots hs,
+                          u64 *er, long long er_cap, int init) {
     if (*(volatile int *)&ctl->skip) return;
     __shared__ HotMin hm;
-    // every candidate endpoint's comp / best slots were set up by the kernel
-    // that wrote the candidate (hook_slot_init), so round 0 starts at once;
-    // the round-0 list is the candidate list itself
+    int *const comp = hs.comp;
+    u64 *const best0 = hs.best0, *const best1 = hs.best1;
+    const unsigned ep = ctl->epoch;
     const long long c0 = (long long)ctl->ncand;
     if (gtid() == 0) {
         ctl->cnt[1] = ctl->cnt[2] = 0;
         ctl->flag[0] = ctl->flag[1] = ctl->flag[2] = 0;
     }
     hm_init(hm);
-    __syncthreads();
+    if (init) {
+        // set up each candidate endpoint once (the first lane to stamp it);
+        // with init == 0 the kernel that wrote the candidates did it and
+        // round 0 starts at once
+        for (long long i = gtid(); i < c0; i += gstride()) {
+            hook_slot_init(hs, ca0[i], ep);
+            hook_slot_init(hs, cb0[i], ep);
+        }
+        if (!grid_barrier(ctl, &ctl->bar[1])) return;
+    } else {
+        __syncthreads();
+    }
     int r = 0;
     for (;; ++r) {
         if (r >= MAX_ROUNDS) {
@@ -1119,9 +1152,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS) k_orient(Ctl *ctl, OrientArgs 
     // the path walks after this kernel follow parent pointers one dependent
     // load at a time: pull the forest into L2 now, while the phases below
     // wait at their barriers (one 128-byte line per thread or so)
-    if (ner > 0)
-        for (long long l = gtid(); l < (a.n + 31) / 32; l += gstride())
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.parent + 32 * l));
+    if (ner > 0) l2_prefetch(a.parent, 4 * a.n, gtid(), gstride());
     // (block-uniform loop: the dense ids are reserved once per block)
     for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < 2 * ner; b0 += gstride()) {
         const long long j = b0 + threadIdx.x;
@@ -1612,9 +1643,9 @@ cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_
     return cudaLaunchCooperativeKernel(fn, d.coop_jump, BLK, args, 0, s);
 }
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
-                           int *comp, u64 *best0, u64 *best1, u64 *er, long long er_cap, cudaStream_t s) {
+                           HookSlots hs, u64 *er, long long er_cap, int init, cudaStream_t s) {
     void *args[] = {(void *)&ctl, (void *)&ck0, (void *)&ca0, (void *)&cb0, (void *)&ck1, (void *)&ca1,
-                    (void *)&cb1, (void *)&comp, (void *)&best0, (void *)&best1, (void *)&er, (void *)&er_cap};
+                    (void *)&cb1, (void *)&hs, (void *)&er, (void *)&er_cap, (void *)&init};
     return cudaLaunchCooperativeKernel((const void *)k_boruvka, d.coop_hook, BLK, args, 0, s);
 }
 cudaError_t launch_orient(const Dev &d, Ctl *ctl, OrientArgs a, cudaStream_t s) {

@@ -150,7 +150,12 @@ __global__ void k_fill(const u64 *dkey, const u64 *dslot, long long m, Csr g, In
 
 // ------------------------------------------------------------ per batch
 
-__global__ void k_validate_batch(int n, Ctl *ctl) {
+// Id validation of the batch.  A batch that touches a notable share of the
+// vertices (at least one per 64) also pulls the per-vertex arrays that the
+// next kernel gathers from at random into L2: rep (both operations) and the
+// parent array (delete) or the row offsets (insert), when they fit in L2
+// with room to spare (on larger graphs they would only evict one another).
+__global__ void k_validate_batch(int n, Ctl *ctl, const int *rep, const int *parent, const long long *off) {
     const int *batch = ctl->batch;
     const long long len = ctl->batch_len;
     GS_LOOP(i, 2 * len) {
@@ -160,78 +165,102 @@ __global__ void k_validate_batch(int n, Ctl *ctl) {
             ctl->skip = 1;
         }
     }
+    if (len * 64 >= n && n <= (1 << 23)) {   // (two arrays of at most 32 MB: well inside L2)
+        const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+        l2_prefetch(rep, 4ll * n, t, nt);
+        if (ctl->op == 1) l2_prefetch(parent, 4ll * n, t, nt);
+        else l2_prefetch(off, 8ll * (n + 1), t, nt);
+    }
 }
 
-// Insert (Algorithm 1 with F^ = F, M = B), one thread per batch entry:
-// normalisation (self-loops, repeated pairs and edges already in G are
-// dropped: the first entry of a new edge claims its index slot, any other
-// finds it taken), then the new edge is appended to both CSR rows (lanes of
-// a warp appending to one row share one atomic; a hub row receives many of a
-// batch's edges), or whole to the overflow list when a row is full, and the
-// cross test rep[u] != rep[v] makes a candidate.  With SG (the supergraph
-// variant, Section III-A) a candidate goes into the pair table instead,
-// which keeps the minimum key per pair of trees (one super-edge per pair;
-// k_pairs_compact then lists them); without it (HS, Section III-B) every
-// cross edge is a candidate of the hooking.  No step needs another entry's
-// claim, so claim and append run in one pass.
-template <bool SG>
-__global__ void k_ins(Ctl *ctl, Csr g, Index ix, u64 *ovf, u64 ovf_cap, const int *rep, PairTable pt, u64 *ck,
-                      int *ca, int *cb, u64 cand_cap, HookSlots hs) {
+// Insert, step 1 (batch normalisation): drop self-loops, repeated pairs and
+// edges already in G; claim an index slot for each new edge.
+__global__ void k_ins_claim(Index ix, Ctl *ctl, u64 *nkey, u64 *nslot) {
     if (*(volatile int *)&ctl->skip) return;
-    const unsigned ep = ctl->epoch;
     const int *batch = ctl->batch;
     const long long len = ctl->batch_len;
-    long long loops = 0, drops = 0, kept = 0;
-    // block-uniform loop: the candidate append and the counters are
-    // aggregated per block
+    // block-uniform loop: counters and the list append are aggregated per
+    // block (one atomic per block instead of one per warp)
+    long long loops = 0, drops = 0;
     for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < len; b0 += (long long)gridDim.x * blockDim.x) {
+        const long long i = b0 + threadIdx.x;
+        bool keep = false;
+        u64 key = 0;
+        long long s = -1;
+        if (i < len) {
+            int u = batch[2 * i], v = batch[2 * i + 1];
+            if (u != v) {
+                key = ekey((uint32_t)u, (uint32_t)v);
+                s = index_claim(ix, key);
+                if (s == LLONG_MIN) atomicOr(&ctl->err, ERR_CAPACITY);
+                keep = s >= 0;
+                drops += !keep;
+            } else {
+                ++loops;
+            }
+        }
+        long long p = block_append(&ctl->nb, keep);
+        if (keep) {
+            nkey[p] = key;
+            nslot[p] = (u64)s;
+        }
+    }
+    block_add(&ctl->self_loops, loops);
+    block_add(&ctl->dropped, drops);
+}
+
+// Insert, step 2: append each new edge to both CSR rows (warp-aggregated
+// row cursors are per row, so plain atomics); an edge whose row is full goes
+// whole to the overflow list.  The cross test of the insert case (M = B,
+// Algorithm 1) is fused here: rep[u] != rep[v] makes a candidate.  With SG
+// (the supergraph variant, Section III-A) a candidate goes into the pair
+// table instead, which keeps the minimum key per pair of trees (one
+// super-edge per pair; k_pairs_compact then lists them); without it (HS,
+// Section III-B) every cross edge is a candidate of the hooking.
+template <bool SG>
+__global__ void k_ins_place(const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, Index ix, u64 *ovf, u64 ovf_cap,
+                            const int *rep, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap, HookSlots hs) {
+    if (*(volatile int *)&ctl->skip) return;
+    const unsigned ep = ctl->epoch;
+    long long nb = (long long)ctl->nb;
+    // block-uniform loop: the candidate append is aggregated per block
+    for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < nb; b0 += (long long)gridDim.x * blockDim.x) {
         const long long i = b0 + threadIdx.x;
         bool cross = false;
         int ra = 0, rb = 0;
         u64 k = 0;
-        if (i < len) {
-            const int u = batch[2 * i], v = batch[2 * i + 1];
-            if (u != v) {
-                k = ekey((uint32_t)u, (uint32_t)v);
-                const uint32_t a = klo(k), b = khi(k);
-                // the cross test's gathers and the row bounds go out with
-                // the index probe (independent of it)
-                ra = rep[a];
-                rb = rep[b];
-                const long long oa = g.off[a], ob = g.off[b];
-                const long long capa = g.off[a + 1] - oa, capb = g.off[b + 1] - ob;
-                const long long s = index_claim(ix, k);
-                if (s == LLONG_MIN) atomicOr(&ctl->err, ERR_CAPACITY);
-                if (s >= 0) {
-                    ++kept;
-                    const int pa = row_slot(g.used, (int)a), pb = row_slot(g.used, (int)b);
-                    const bool fa = pa < capa, fb = pb < capb;
-                    if (fa && fb) {
-                        g.col[oa + pa] = (int)b;
-                        g.col[ob + pb] = (int)a;
-                        ix.pu[s] = (uint32_t)(oa + pa);
-                        ix.pv[s] = (uint32_t)(ob + pb);
-                    } else {
-                        // the consumed free slot (if any) stays -1
-                        const u64 o = atomicAdd(&ctl->ovf_count, 1ull);
-                        if (o < ovf_cap) {
-                            ovf[o] = k;
-                            ix.pu[s] = POS_OVF;
-                            ix.pv[s] = (uint32_t)o;
-                        } else {
-                            atomicOr(&ctl->err, ERR_CAPACITY);
-                        }
-                        atomicAdd((u64 *)&ctl->overflow_total, 1ull);
-                        if (fa || fb) atomicAdd((u64 *)&ctl->ctomb, 1ull);
-                    }
-                    cross = ra != rb;
-                    if (SG && cross) cross = !pair_min(pt.pk, pt.mk, pt.mask, ra, rb, k);   // no slot: plain candidate
-                } else {
-                    ++drops;
-                }
+        if (i < nb) {
+            k = nkey[i];
+            u64 s = nslot[i];
+            uint32_t a = klo(k), b = khi(k);
+            long long oa = g.off[a], ob = g.off[b];
+            long long capa = g.off[a + 1] - oa, capb = g.off[b + 1] - ob;
+            // lanes appending to the same row take consecutive slots from one
+            // atomic (a hub row receives many of a batch's edges)
+            int pa = row_slot(g.used, (int)a), pb = row_slot(g.used, (int)b);
+            bool fa = pa < capa, fb = pb < capb;
+            if (fa && fb) {
+                g.col[oa + pa] = (int)b;
+                g.col[ob + pb] = (int)a;
+                ix.pu[s] = (uint32_t)(oa + pa);
+                ix.pv[s] = (uint32_t)(ob + pb);
             } else {
-                ++loops;
+                // the consumed free slot (if any) stays -1
+                u64 o = atomicAdd(&ctl->ovf_count, 1ull);
+                if (o < ovf_cap) {
+                    ovf[o] = k;
+                    ix.pu[s] = POS_OVF;
+                    ix.pv[s] = (uint32_t)o;
+                } else {
+                    atomicOr(&ctl->err, ERR_CAPACITY);
+                }
+                atomicAdd((u64 *)&ctl->overflow_total, 1ull);
+                if (fa || fb) atomicAdd((u64 *)&ctl->ctomb, 1ull);
             }
+            ra = rep[a];
+            rb = rep[b];
+            cross = ra != rb;
+            if (SG && cross) cross = !pair_min(pt.pk, pt.mk, pt.mask, ra, rb, k);   // no slot: plain candidate
         }
         long long p = block_append(&ctl->ncand, cross);
         if (cross) {
@@ -239,17 +268,18 @@ __global__ void k_ins(Ctl *ctl, Csr g, Index ix, u64 *ovf, u64 ovf_cap, const in
                 ck[p] = k;
                 ca[p] = ra;
                 cb[p] = rb;
-                hook_slot_init(hs, ra, ep);
-                hook_slot_init(hs, rb, ep);
+                // HS: these are all the candidates, so the hooking needs no
+                // initialisation phase of its own (see HookSlots)
+                if (!SG) {
+                    hook_slot_init(hs, ra, ep);
+                    hook_slot_init(hs, rb, ep);
+                }
             } else {
                 atomicOr(&ctl->err, ERR_CAPACITY);
             }
         }
     }
-    block_add(&ctl->self_loops, loops);
-    block_add(&ctl->dropped, drops);
-    block_add((long long *)&ctl->nb, kept);
-    block_add(&ctl->edges, kept);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((u64 *)&ctl->edges, (u64)nb);
 }
 
 // Delete, step 1: normalisation (absent edges and repeats dropped), removal
@@ -349,9 +379,8 @@ __global__ void k_del_claim(Index ix, Csr g, u64 *ovf, int *parent, const int *r
 // Entry positions are below 2^32, so the tile arithmetic is 32-bit.
 template <bool SG>
 __global__ void k_scan_lb(RowList rl, Ctl *ctl, Csr g, const int *rep, PairTable pt, u64 *ck, int *ca, int *cb,
-                          u64 cand_cap, HookSlots hs) {
+                          u64 cand_cap) {
     if (*(volatile int *)&ctl->skip) return;
-    const unsigned ep = ctl->epoch;
     const unsigned nd = (unsigned)ctl->ndet;
     if (nd == 0) return;
     const unsigned E = rl.roff[nd];
@@ -435,8 +464,6 @@ __global__ void k_scan_lb(RowList rl, Ctl *ctl, Csr g, const int *rep, PairTable
                 ck[p] = key;
                 ca[p] = ru;
                 cb[p] = rx;
-                hook_slot_init(hs, ru, ep);
-                hook_slot_init(hs, rx, ep);
             } else {
                 atomicOr(&ctl->err, ERR_CAPACITY);
             }
@@ -449,9 +476,8 @@ __global__ void k_scan_lb(RowList rl, Ctl *ctl, Csr g, const int *rep, PairTable
 // through the same pair table (SG) or straight to the candidates (HS).
 template <bool SG>
 __global__ void k_scan_ovf(const u64 *ovf, Ctl *ctl, const int *rep, PairTable pt, u64 *ck, int *ca, int *cb,
-                           u64 cand_cap, HookSlots hs) {
+                           u64 cand_cap) {
     if (*(volatile int *)&ctl->skip) return;
-    const unsigned ep = ctl->epoch;
     long long no = (long long)ctl->ovf_count;
     GS_LOOP(i, no) {
         u64 k = ovf[i];
@@ -468,8 +494,6 @@ __global__ void k_scan_ovf(const u64 *ovf, Ctl *ctl, const int *rep, PairTable p
                 ck[p] = k;
                 ca[p] = ra;
                 cb[p] = rb;
-                hook_slot_init(hs, ra, ep);
-                hook_slot_init(hs, rb, ep);
             } else {
                 atomicOr(&ctl->err, ERR_CAPACITY);
             }
@@ -479,9 +503,8 @@ __global__ void k_scan_ovf(const u64 *ovf, Ctl *ctl, const int *rep, PairTable p
 
 // Move the pair table into the candidate list (one candidate per piece
 // pair, its minimum key) and free the slots for the next batch.
-__global__ void k_pairs_compact(Ctl *ctl, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap, HookSlots hs) {
+__global__ void k_pairs_compact(Ctl *ctl, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap) {
     if (*(volatile int *)&ctl->skip) return;
-    const unsigned ep = ctl->epoch;
     // four slots per thread and iteration, one counter reservation per
     // block (the table has far more slots than warps have lanes, and most
     // warps hold an occupied slot: a per-warp append would queue on the
@@ -513,12 +536,9 @@ __global__ void k_pairs_compact(Ctl *ctl, PairTable pt, u64 *ck, int *ca, int *c
         for (int q = 0; q < 4; ++q) {
             if (!on[q]) continue;
             if ((u64)p[q] < cand_cap) {
-                const int a = (int)(pair[q] >> 32), b = (int)(pair[q] & 0xFFFFFFFFu);
                 ck[p[q]] = k[q];
-                ca[p[q]] = a;
-                cb[p[q]] = b;
-                hook_slot_init(hs, a, ep);
-                hook_slot_init(hs, b, ep);
+                ca[p[q]] = (int)(pair[q] >> 32);
+                cb[p[q]] = (int)(pair[q] & 0xFFFFFFFFu);
             } else {
                 atomicOr(&ctl->err, ERR_CAPACITY);
             }
@@ -620,16 +640,24 @@ cudaError_t launch_fill(const u64 *dkey, const u64 *dslot, long long m, Csr g, I
 }
 // The batch kernels read the batch and its length from the control block;
 // `len` only sizes their grid (a captured launch sequence is keyed by it).
-cudaError_t launch_validate_batch(long long len, int n, Ctl *ctl, cudaStream_t s) {
-    k_validate_batch<<<gsz(2 * len), BLK, 0, s>>>(n, ctl);
+cudaError_t launch_validate_batch(long long len, int n, Ctl *ctl, const int *rep, const int *parent,
+                                  const long long *off, cudaStream_t s) {
+    k_validate_batch<<<gsz(2 * len), BLK, 0, s>>>(n, ctl, rep, parent, off);
     return cudaGetLastError();
 }
-cudaError_t launch_ins(long long len, Ctl *ctl, Csr g, Index ix, u64 *ovf, u64 ovf_cap, const int *rep, bool sg,
-                       PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap, HookSlots hs, cudaStream_t s) {
+cudaError_t launch_ins_claim(long long len, Index ix, Ctl *ctl, u64 *nkey, u64 *nslot, cudaStream_t s) {
+    k_ins_claim<<<gsz(len), BLK, 0, s>>>(ix, ctl, nkey, nslot);
+    return cudaGetLastError();
+}
+cudaError_t launch_ins_place(const Dev &d, const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, Index ix,
+                             u64 *ovf, u64 ovf_cap, const int *rep, bool sg, PairTable pt, u64 *ck, int *ca, int *cb,
+                             u64 cand_cap, HookSlots hs, cudaStream_t s) {
     if (sg)
-        k_ins<true><<<gsz(len), BLK, 0, s>>>(ctl, g, ix, ovf, ovf_cap, rep, pt, ck, ca, cb, cand_cap, hs);
+        k_ins_place<true><<<d.grid, BLK, 0, s>>>(nkey, nslot, ctl, g, ix, ovf, ovf_cap, rep, pt, ck, ca, cb, cand_cap,
+                                                 hs);
     else
-        k_ins<false><<<gsz(len), BLK, 0, s>>>(ctl, g, ix, ovf, ovf_cap, rep, pt, ck, ca, cb, cand_cap, hs);
+        k_ins_place<false><<<d.grid, BLK, 0, s>>>(nkey, nslot, ctl, g, ix, ovf, ovf_cap, rep, pt, ck, ca, cb,
+                                                  cand_cap, hs);
     return cudaGetLastError();
 }
 cudaError_t launch_del_claim(long long len, Index ix, Csr g, u64 *ovf, int *parent, const int *rep, Ctl *ctl,
@@ -639,11 +667,11 @@ cudaError_t launch_del_claim(long long len, Index ix, Csr g, u64 *ovf, int *pare
     return cudaGetLastError();
 }
 cudaError_t launch_scan_rows(const Dev &d, RowList rl, Ctl *ctl, Csr g, const int *rep, bool sg, PairTable pt,
-                             u64 *ck, int *ca, int *cb, u64 cand_cap, HookSlots hs, cudaStream_t s) {
+                             u64 *ck, int *ca, int *cb, u64 cand_cap, cudaStream_t s) {
     if (sg)
-        k_scan_lb<true><<<d.grid_scan, BLK, 0, s>>>(rl, ctl, g, rep, pt, ck, ca, cb, cand_cap, hs);
+        k_scan_lb<true><<<d.grid_scan, BLK, 0, s>>>(rl, ctl, g, rep, pt, ck, ca, cb, cand_cap);
     else
-        k_scan_lb<false><<<d.grid_scan, BLK, 0, s>>>(rl, ctl, g, rep, pt, ck, ca, cb, cand_cap, hs);
+        k_scan_lb<false><<<d.grid_scan, BLK, 0, s>>>(rl, ctl, g, rep, pt, ck, ca, cb, cand_cap);
     return cudaGetLastError();
 }
 // Every warp of the row scan takes an equal share of the tiles, so the grid
@@ -656,17 +684,17 @@ unsigned scan_grid(int nsm) {
     return (unsigned)(per * nsm);
 }
 cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, bool sg, PairTable pt, u64 *ck,
-                            int *ca, int *cb, u64 cand_cap, HookSlots hs, cudaStream_t s) {
+                            int *ca, int *cb, u64 cand_cap, cudaStream_t s) {
     if (sg)
-        k_scan_ovf<true><<<d.nsm * 2, BLK, 0, s>>>(ovf, ctl, rep, pt, ck, ca, cb, cand_cap, hs);
+        k_scan_ovf<true><<<d.nsm * 2, BLK, 0, s>>>(ovf, ctl, rep, pt, ck, ca, cb, cand_cap);
     else
-        k_scan_ovf<false><<<d.nsm * 2, BLK, 0, s>>>(ovf, ctl, rep, pt, ck, ca, cb, cand_cap, hs);
+        k_scan_ovf<false><<<d.nsm * 2, BLK, 0, s>>>(ovf, ctl, rep, pt, ck, ca, cb, cand_cap);
     return cudaGetLastError();
 }
 cudaError_t launch_pairs_compact(const Dev &d, Ctl *ctl, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap,
-                                 HookSlots hs, cudaStream_t s) {
+                                 cudaStream_t s) {
     k_pairs_compact<<<grid_for(((long long)pt.mask + 4) / 4, BLK, (unsigned)d.nsm * 8u), BLK, 0, s>>>(ctl, pt, ck, ca,
-                                                                                                   cb, cand_cap, hs);
+                                                                                                   cb, cand_cap);
     return cudaGetLastError();
 }
 cudaError_t launch_extract(const Dev &d, int n, Csr g, const u64 *ovf, u64 novf_max, Ctl *ctl, int *out,

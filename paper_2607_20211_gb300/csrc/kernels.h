@@ -31,7 +31,8 @@ cudaError_t launch_caps(const int *deg, int n, long long *cap, cudaStream_t s);
 cudaError_t launch_scan_i64(const long long *in, long long *out, long long n, long long *bsum, cudaStream_t s);
 cudaError_t launch_fill(const u64 *dkey, const u64 *dslot, long long m, Csr g, Index ix, cudaStream_t s);
 // (the batch kernels read the batch from the control block; len sizes the grid)
-cudaError_t launch_validate_batch(long long len, int n, Ctl *ctl, cudaStream_t s);
+cudaError_t launch_validate_batch(long long len, int n, Ctl *ctl, const int *rep, const int *parent,
+                                  const long long *off, cudaStream_t s);
 
 cudaError_t launch_del_claim(long long len, Index ix, Csr g, u64 *ovf, int *parent, const int *rep, Ctl *ctl,
                              unsigned *aff_ep, unsigned *cut_ep, int *cutlist, unsigned *w, int *rold,
@@ -55,15 +56,17 @@ struct PairTable {
 };
 // sg: supergraph variant (pair-table dedupe to one minimum-key edge per
 // pair of trees), else every cross edge is a candidate (hooking variant)
-// insert: normalisation, index claim, CSR append and cross test in one pass
-cudaError_t launch_ins(long long len, Ctl *ctl, Csr g, Index ix, u64 *ovf, u64 ovf_cap, const int *rep, bool sg,
-                       PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap, HookSlots hs, cudaStream_t s);
+cudaError_t launch_ins_claim(long long len, Index ix, Ctl *ctl, u64 *nkey, u64 *nslot, cudaStream_t s);
+// (HS: the candidates' hook-forest slots are set up here, see HookSlots)
+cudaError_t launch_ins_place(const Dev &d, const u64 *nkey, const u64 *nslot, Ctl *ctl, Csr g, Index ix,
+                             u64 *ovf, u64 ovf_cap, const int *rep, bool sg, PairTable pt, u64 *ck, int *ca, int *cb,
+                             u64 cand_cap, HookSlots hs, cudaStream_t s);
 cudaError_t launch_scan_rows(const Dev &d, RowList rl, Ctl *ctl, Csr g, const int *rep, bool sg, PairTable pt,
-                             u64 *ck, int *ca, int *cb, u64 cand_cap, HookSlots hs, cudaStream_t s);
+                             u64 *ck, int *ca, int *cb, u64 cand_cap, cudaStream_t s);
 cudaError_t launch_scan_ovf(const Dev &d, const u64 *ovf, Ctl *ctl, const int *rep, bool sg, PairTable pt, u64 *ck,
-                            int *ca, int *cb, u64 cand_cap, HookSlots hs, cudaStream_t s);
+                            int *ca, int *cb, u64 cand_cap, cudaStream_t s);
 cudaError_t launch_pairs_compact(const Dev &d, Ctl *ctl, PairTable pt, u64 *ck, int *ca, int *cb, u64 cand_cap,
-                                 HookSlots hs, cudaStream_t s);
+                                 cudaStream_t s);
 cudaError_t launch_extract(const Dev &d, int n, Csr g, const u64 *ovf, u64 novf_max, Ctl *ctl, int *out,
                            long long cap, u64 *cnt, cudaStream_t s);
 cudaError_t launch_check_tree_edges(int n, const int *parent, Index ix, int *bad, cudaStream_t s);
@@ -75,7 +78,11 @@ cudaError_t launch_aff_collect(const Dev &d, int n, const int *rep, const unsign
                                unsigned *w, u64 *heavy, Ctl *ctl, const int *par, int *J, int roots_only,
                                cudaStream_t s);
 // delete: detached vertices top-down from the cut vertices (falls back to
-// the pointer jumping above when over budget); root pieces to list after it
+// the pointer jumping above when over budget); root pieces to list after it.
+// DETACH_LEVELS: its level limit (measured on R-MAT, where it pays, the
+// search takes 2-7 levels; on deep trees each level costs about as much as
+// a whole pointer-jumping round)
+#define DETACH_LEVELS 16
 cudaError_t launch_detach(const Dev &d, Ctl *ctl, const int *cuts, const int *par, int *rep, Csr g, const u64 *ovf,
                           u64 ovf_cap, RowList rl, int *A, int *J1, unsigned *det_ep, unsigned *det_claim,
                           const int *rold, long long budget_v, long long budget_e, int max_levels, int *oc, int *op,
@@ -87,9 +94,9 @@ cudaError_t launch_jump_async(const Dev &d, const int *A, Ctl *ctl, int *J, int 
 cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, const int *par,
                         int *J, int *J1, int *rep, RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy,
                         Csr g, int sync_rounds, int *X, int *Y, const int *cuts, cudaStream_t s);
-// (the candidates' writers set up the endpoints' comp / best slots: HookSlots)
+// init: set up the candidates' endpoints first (0: their writer did, HookSlots)
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
-                           int *comp, u64 *best0, u64 *best1, u64 *er, long long er_cap, cudaStream_t s);
+                           HookSlots hs, u64 *er, long long er_cap, int init, cudaStream_t s);
 struct OrientArgs {
     const u64 *er;
     const int *rep;
