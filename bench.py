@@ -430,6 +430,34 @@ def run_ours(args, rank, ws, local):
         e2e = {"value": round(eu / es, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d // K),
                "d2h_bytes_per_step": 152, "ms_per_step": round(tt / K * 1e3, 4),
                "path": "drsf_apply_host (pinned staging) + drsf_stats read-back"}
+        # the same steps with the whole updated forest F' read back to the
+        # host every step (drsf_parent into a device buffer, then one copy
+        # to pinned host memory): the full host-visible cost of an update
+        f = drsf.DynamicForest(g.n, edges_d, parent_d)
+        pbuf = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        phost = torch.empty(g.n, dtype=torch.int32, pin_memory=True)
+        for s in range(W):
+            for op in (0, 1):
+                f.apply_host(op, host[s][op])
+        f.stats()
+        barrier()
+        tp = 0.0
+        for k in range(K):
+            t0 = time.perf_counter()
+            f.apply_host(0, host[W + k][0])
+            f.apply_host(1, host[W + k][1])
+            st = f.stats()
+            phost.copy_(f.parent(pbuf), non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            tp += time.perf_counter() - t0
+        barrier()
+        if not np.array_equal(phost.numpy(), final_plan):
+            raise RuntimeError("e2e replay with read-back diverged from the planning pass")
+        f.close()
+        pu, ps = aggregate(float(applied_i + applied_d), tp)
+        e2e["with_parent_readback"] = {"value": round(pu / ps, 1), "unit": UNIT, "ms_per_step": round(tp / K * 1e3, 4),
+                                       "d2h_bytes_per_step": 152 + 4 * g.n,
+                                       "path": "the same + drsf_parent and a copy of F' to pinned host memory"}
     clocks = clk.stop()
 
     cpu = None

@@ -629,6 +629,7 @@ drsf_status drsf_create(int32_t n, const int32_t *edges, int64_t m, const int32_
     h->dev.coop_bfs = coop_blocks_bfs(nsm);
     h->dev.grid_scan = scan_grid(nsm);
     h->dev.grid_pass = grid_vertex_pass(nsm);
+    h->dev.grid_list = grid_list_pass(nsm);
     h->dev.coop_et = coop_blocks_et(nsm);
     h->dev.coop_detach = coop_blocks_detach(nsm);
     // root search of a delete batch: barrier-free doubling over per-warp

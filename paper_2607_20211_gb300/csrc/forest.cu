@@ -36,6 +36,10 @@
 // passes are one dependent gather behind a streaming load)
 #define IPT 4
 #define IPN 16
+// k_aff_collect keeps more per item (old root, list position): 8 items per
+// thread (48 registers) measured faster than 16 (64 registers, fewer
+// resident blocks): 0.036 vs 0.041 ms per pass on R-MAT scale 22
+#define IPA 8
 // top-down delete: after a search that gave up at its level limit, the
 // deletes that skip it before it is tried again
 #define DETACH_BACKOFF 8
@@ -127,25 +131,25 @@ __global__ void k_begin(Ctl *ctl, int op, long long len, const int *batch) {
 __global__ void __launch_bounds__(BLK) k_aff_collect(int n, const int *rep, const unsigned *aff_ep, int *A, int *rold,
                                                      unsigned *w, u64 *heavy, Ctl *ctl, const int *par, int *J,
                                                      int roots_only) {
-    static_assert(IPN <= 32, "item masks are 32 bits");
+    static_assert(IPA <= 32, "item masks are 32 bits");
     if (*(volatile int *)&ctl->skip) return;
     if (roots_only ? !(*(volatile int *)&ctl->td && *(volatile int *)&ctl->need_root) : *(volatile int *)&ctl->td)
         return;
     unsigned ep = ctl->epoch;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const long long step = (long long)gridDim.x * blockDim.x * IPN;
-    for (long long b0 = (long long)blockIdx.x * blockDim.x * IPN; b0 < n; b0 += step) {
+    const long long step = (long long)gridDim.x * blockDim.x * IPA;
+    for (long long b0 = (long long)blockIdx.x * blockDim.x * IPA; b0 < n; b0 += step) {
         const long long v0 = b0 + threadIdx.x;
-        int r[IPN];
+        int r[IPA];
 #pragma unroll
-        for (int k = 0; k < IPN; ++k) {
+        for (int k = 0; k < IPA; ++k) {
             const long long v = v0 + (long long)k * blockDim.x;
             r[k] = v < n ? rep[v] : 0;
         }
         unsigned in = 0;
 #pragma unroll
-        for (int k = 0; k < IPN; ++k) {
+        for (int k = 0; k < IPA; ++k) {
             const long long v = v0 + (long long)k * blockDim.x;
             if (v < n && aff_ep[r[k]] == ep) in |= 1u << k;
         }
@@ -154,7 +158,7 @@ __global__ void __launch_bounds__(BLK) k_aff_collect(int n, const int *rep, cons
         long long p = block_reserve(&ctl->naff, lane == 0 ? tot : 0);
         p = __shfl_sync(0xffffffffu, p, 0);
 #pragma unroll
-        for (int k = 0; k < IPN; ++k) {
+        for (int k = 0; k < IPA; ++k) {
             const unsigned bk = __ballot_sync(0xffffffffu, (in >> k) & 1u);
             if ((in >> k) & 1u) {
                 const int v = (int)(v0 + (long long)k * blockDim.x);
@@ -1576,11 +1580,10 @@ static unsigned coop_blocks(const void *fn, int nsm, int cap_per_sm) {
 // The vertex passes (k_aff_collect, k_active) loop over their range with
 // the blocks that are resident at once: no partial last wave.
 unsigned grid_vertex_pass(int nsm) {
-    unsigned a = coop_blocks((const void *)k_aff_collect, nsm, 8),
-             b = coop_blocks((const void *)k_active<IPN>, nsm, 8),
-             c = coop_blocks((const void *)k_active<IPT>, nsm, 8);
-    return a < b ? (a < c ? a : c) : (b < c ? b : c);
+    unsigned a = coop_blocks((const void *)k_aff_collect, nsm, 8), b = coop_blocks((const void *)k_active<IPN>, nsm, 8);
+    return a < b ? a : b;
 }
+unsigned grid_list_pass(int nsm) { return coop_blocks((const void *)k_active<IPT>, nsm, 8); }
 unsigned coop_blocks_jump(int nsm) {
     // the three root-search variants share one launch bound; take the least
     unsigned a = coop_blocks((const void *)k_jump<0>, nsm, 8), b = coop_blocks((const void *)k_jump<1>, nsm, 8),
@@ -1663,7 +1666,7 @@ cudaError_t launch_active(const Dev &d, const int *L, int use_list, long long cn
                           const int *newrep, int *act, int *pold, int *J0, unsigned char *mark, int *aidx,
                           int *aroot, cudaStream_t s) {
     if (use_list)
-        k_active<IPT><<<d.grid_pass, BLK, 0, s>>>(L, use_list, cnt_static, ctl, rep, parent, sel_ep, att_x, rep_ep,
+        k_active<IPT><<<d.grid_list, BLK, 0, s>>>(L, use_list, cnt_static, ctl, rep, parent, sel_ep, att_x, rep_ep,
                                                   newrep, act, pold, J0, mark, aidx, aroot);
     else
         k_active<IPN><<<d.grid_pass, BLK, 0, s>>>(L, use_list, cnt_static, ctl, rep, parent, sel_ep, att_x, rep_ep,

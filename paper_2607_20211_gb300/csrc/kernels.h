@@ -18,7 +18,8 @@ struct Dev {
     unsigned coop_et;
     unsigned coop_detach;
     unsigned grid_scan;   // row scan: the co-resident block count
-    unsigned grid_pass;   // vertex passes (affected list, refresh): the co-resident block count
+    unsigned grid_pass;   // passes over all n vertices (affected list, insert refresh): co-resident blocks
+    unsigned grid_list;   // passes over a vertex list (delete refresh): co-resident blocks
 };
 
 // graph.cu -------------------------------------------------------------
@@ -131,6 +132,7 @@ cudaError_t launch_labels(int n, const int *rep, int *tmp, int *out, cudaStream_
 
 unsigned coop_blocks_jump(int nsm);
 unsigned grid_vertex_pass(int nsm);
+unsigned grid_list_pass(int nsm);
 unsigned coop_blocks_hook(int nsm);
 unsigned coop_blocks_orient(int nsm);
 unsigned coop_blocks_mark(int nsm);
