@@ -275,3 +275,27 @@ def test_top_down_detach_and_its_fallback(monkeypatch):
     assert seen["top"] > 0 and seen["fallback"] > 0, seen
     monkeypatch.setenv("DRSF_DETACH", "0")
     run_trajectory(workloads.rmat_graph(16, 16, seed=2), [(I, 1000), (D, 1000), (I, 10_000), (D, 10_000)], seed=3)
+
+
+def test_top_down_level_limit_skip_and_retry():
+    """A path of 20,000 vertices rooted at 0: every cut detaches a chain far
+    deeper than the top-down search's level limit (16), and small enough for
+    its vertex and entry budgets, so the search gives up at the limit
+    (detach_levels == -16), the next 8 deletes skip it (detach_levels == 0:
+    pointer jumping from the start), and the one after tries it again.
+    Every batch matches the oracle."""
+    n = 20_000
+    edges = [(i, i + 1) for i in range(n - 1)]
+    g = _tiny(n, edges, [0] + list(range(n - 1)))
+    f = make_forest(g)
+    keys, par = g.keys, g.parent
+    levels = []
+    try:
+        for b in range(10):
+            k = 100 * (b + 1)
+            keys, par, st = check_batch(f, n, keys, par, D, np.array([[k, k + 1]], np.int32))
+            assert st["tree_cut"] == 1
+            levels.append(st["detach_levels"])
+    finally:
+        f.close()
+    assert levels == [-16] + [0] * 8 + [-16], levels
