@@ -1080,19 +1080,19 @@ __device__ int rank_block(Ctl *ctl, int *svc, int *svn, int *snc, int *snn, int 
 // of each core piece, arcs placed, Euler successors (as in the grid phases
 // of k_orient) written straight into shared memory, ranked there, and each
 // core edge oriented by its arc that comes first.  Block barriers only.
-__device__ void orient_small_core(Ctl *ctl, const OrientArgs &a, long long nce, unsigned ep) {
+__device__ void orient_small_core(Ctl *ctl, const OrientArgs &a, const int *cel, long long nce, unsigned ep) {
     __shared__ int s_nc;
     if (threadIdx.x == 0) s_nc = 0;
     __syncthreads();
     for (long long t = threadIdx.x; t < 2 * nce; t += blockDim.x) {
-        const long long j = 2 * (long long)LD(a.cel[t >> 1]) + (t & 1);
+        const long long j = 2 * (long long)LD(cel[t >> 1]) + (t & 1);
         const int id = LD(a.eid[j]);
         if (atomicCAS(&a.poff[id], -1, -2) == -1) a.poff[id] = atomicAdd(&s_nc, LD(a.cdeg[id]));
     }
     __syncthreads();
     const int ncore = s_nc;
     for (long long t = threadIdx.x; t < 2 * nce; t += blockDim.x) {
-        const long long j = 2 * (long long)LD(a.cel[t >> 1]) + (t & 1);
+        const long long j = 2 * (long long)LD(cel[t >> 1]) + (t & 1);
         const int id = LD(a.eid[j]);
         const int slot = a.poff[id] + atomicAdd(&a.pcur[id], 1);
         a.adj[slot] = (int)j;
@@ -1102,7 +1102,7 @@ __device__ void orient_small_core(Ctl *ctl, const OrientArgs &a, long long nce, 
     extern __shared__ int s_rank[];
     int *svc = s_rank, *svn = svc + ORIENT_SMEM_ARCS, *snc = svn + ORIENT_SMEM_ARCS, *snn = snc + ORIENT_SMEM_ARCS;
     for (long long t = threadIdx.x; t < 2 * nce; t += blockDim.x) {
-        const long long j = 2 * (long long)LD(a.cel[t >> 1]) + (t & 1);
+        const long long j = 2 * (long long)LD(cel[t >> 1]) + (t & 1);
         const long long tw = j ^ 1;
         const int hid = LD(a.eid[tw]);   // the arc's head = the twin's source
         const int start = a.poff[hid], end = start + LD(a.cdeg[hid]);
@@ -1122,7 +1122,7 @@ __device__ void orient_small_core(Ctl *ctl, const OrientArgs &a, long long nce, 
     int *rank = nullptr;
     const int rounds = rank_block(ctl, svc, svn, snc, snn, ncore, &rank);
     for (long long t = threadIdx.x; t < nce; t += blockDim.x) {
-        const long long i = LD(a.cel[t]);
+        const long long i = LD(cel[t]);
         orient_one(a, i, rank[a.apos[2 * i]] > rank[a.apos[2 * i + 1]], ep);
     }
     if (threadIdx.x == 0) {
@@ -1152,7 +1152,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS) k_orient(Ctl *ctl, OrientArgs 
     // (ep), later phases its dense id (eid) and each edge's super-tree root
     // (eroot), so no phase re-walks rep / pidx / the hook forest.
     // phase 1: dense ids for the pieces touched by E_r
-    if (gtid() == 0) ctl->ncore = ctl->cnt[0] = 0;
+    if (gtid() == 0) ctl->ncore = ctl->cnt[0] = ctl->cnt[1] = 0;
     // the path walks after this kernel follow parent pointers one dependent
     // load at a time: pull the forest into L2 now, while the phases below
     // wait at their barriers (one 128-byte line per thread or so)
@@ -1230,17 +1230,62 @@ __global__ void __launch_bounds__(ORIENT_THREADS) k_orient(Ctl *ctl, OrientArgs 
     }
     if (!grid_barrier(ctl, bar)) return;
     {
-        // A small core (most batches: the leaves are most of E_r) is done by
-        // block 0 alone with block barriers (adjacency, Euler successors,
-        // ranking in shared memory, orientation), while every block orients
-        // the leaf edges; a large one takes the grid phases below.
-        const long long nce = (long long)*(volatile u64 *)&ctl->cnt[0];
+        // A small core (small batches: tens of edges) is done by block 0
+        // alone with block barriers (adjacency, Euler successors, ranking in
+        // shared memory, orientation), while every block orients the leaf
+        // edges.  A larger one first gets a second round of leaf raking
+        // (phase 2c: on R-MAT it leaves about a tenth of the core), and
+        // takes the grid phases below only if it is still large.
+        long long nce = (long long)*(volatile u64 *)&ctl->cnt[0];
+        const int *cel = a.cel;
+        if (nce > ORIENT_SMALL_EDGES) {
+            // phase 2c: a core piece with a single core edge that is not its
+            // super-tree's root is a leaf of the remaining core; its edge is
+            // oriented towards the other piece (lf) and both core degrees
+            // drop.  Core degrees only fall, so a stale read can miss a leaf
+            // but never make one up (the edge being looked at is still
+            // alive, so a degree read as 1 is exactly 1), and both ends of
+            // one edge cannot be such leaves (every core component holds its
+            // root).  The edges left are listed again (second half of cel).
+            int *cel2 = a.cel + ner;
+            for (long long b0 = gtid() & ~31ll; b0 < nce; b0 += gstride()) {
+                const long long t = b0 + (threadIdx.x & 31);
+                bool keep = false;
+                long long i = 0;
+                if (t < nce) {
+                    i = LD(a.cel[t]);
+                    const int id0 = LD(a.eid[2 * i]), id1 = LD(a.eid[2 * i + 1]);
+                    const int p0 = LD(a.ep[2 * i]), p1 = LD(a.ep[2 * i + 1]);
+                    const int sr = LD(a.minp[LD(a.eroot[i])]);
+                    const bool l0 = LD(a.cdeg[id0]) == 1 && p0 != sr;
+                    const bool l1 = !l0 && LD(a.cdeg[id1]) == 1 && p1 != sr;
+                    if (l0 || l1) {
+                        a.lf[i] = l0 ? 1 : 2;
+                        atomicSub(&a.cdeg[id0], 1);
+                        atomicSub(&a.cdeg[id1], 1);
+                    } else {
+                        keep = true;
+                    }
+                }
+                const unsigned km = __ballot_sync(0xffffffffu, keep);
+                if (km) {
+                    const int lane = threadIdx.x & 31, ld = __ffs(km) - 1;
+                    u64 q0 = 0;
+                    if (lane == ld) q0 = atomicAdd(&ctl->cnt[1], (u64)__popc(km));
+                    q0 = __shfl_sync(0xffffffffu, q0, ld);
+                    if (keep) cel2[q0 + __popc(km & ((1u << lane) - 1u))] = (int)i;
+                }
+            }
+            if (!grid_barrier(ctl, bar)) return;
+            nce = (long long)*(volatile u64 *)&ctl->cnt[1];
+            cel = cel2;
+        }
         if (nce <= ORIENT_SMALL_EDGES) {
             for (long long i = gtid(); i < ner; i += gstride()) {
                 const unsigned char lf = LD(a.lf[i]);
                 if (lf) orient_one(a, i, lf == 2, ep);
             }
-            if (blockIdx.x == 0) orient_small_core(ctl, a, nce, ep);
+            if (blockIdx.x == 0) orient_small_core(ctl, a, cel, nce, ep);
             return;
         }
     }
