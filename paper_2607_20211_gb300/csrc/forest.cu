@@ -21,6 +21,10 @@
 #define ORIENT_SMEM_ARCS 12288
 #define ORIENT_SMEM_BYTES (4 * ORIENT_SMEM_ARCS * (int)sizeof(int))
 #define ORIENT_THREADS 1024
+// hooking: threads per block (one block per SM) and the live candidates at
+// the start of a round (after round 0) up to which block 0 finishes alone
+#define HOOK_THREADS 1024
+#define HOOK_TAIL 8192
 // a core of at most this many edges is oriented by one block (measured on
 // R-MAT-22: faster than the grid phases for small batches' cores of tens of
 // edges, slower for the 100K batches' cores of about 900 edges)
@@ -922,48 +926,37 @@ __device__ __forceinline__ void hm_flush(HotMin &t, u64 *arr, u64 *rst_arr) {
 // component are dropped, the rest are compacted for the next round.  With
 // distinct keys this is Boruvka's algorithm: E_r is the unique minimum
 // spanning forest of the piece multigraph, |E_r| = k - l.
-__global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1, HookSlots hs,
-                          u64 *er, long long er_cap, int init) {
-    if (*(volatile int *)&ctl->skip) return;
-    __shared__ HotMin hm;
-    int *const comp = hs.comp;
-    u64 *const best0 = hs.best0, *const best1 = hs.best1;
-    const unsigned ep = ctl->epoch;
-    const long long c0 = (long long)ctl->ncand;
-    if (gtid() == 0) {
-        ctl->cnt[1] = ctl->cnt[2] = 0;
-        ctl->flag[0] = ctl->flag[1] = ctl->flag[2] = 0;
-    }
-    hm_init(hm);
-    if (init) {
-        // set up each candidate endpoint once (the first lane to stamp it);
-        // with init == 0 the kernel that wrote the candidates did it and
-        // round 0 starts at once
-        for (long long i = gtid(); i < c0; i += gstride()) {
-            hook_slot_init(hs, ca0[i], ep);
-            hook_slot_init(hs, cb0[i], ep);
-        }
-        if (!grid_barrier(ctl, &ctl->bar[1])) return;
-    } else {
-        __syncthreads();
-    }
-    int r = 0;
+// Rounds r, r+1, ... of the hook-and-compress, by the whole grid (ONE
+// false: grid barriers between phases) or by block 0 alone (ONE true: block
+// barriers).  On the grid, a round that starts with at most HOOK_TAIL live
+// candidates (after round 0 on R-MAT batches: about 2.5% of them) is handed
+// to block 0: every block reads the same count after the barrier, so all
+// take that branch together.  Returns -1 when a grid barrier gave up, the
+// round to hand to block 0 (grid only), or 0 when done.
+template <bool ONE>
+__device__ __forceinline__ int hook_rounds(Ctl *ctl, HotMin &hm, int r, long long c0, u64 *ck0, int *ca0, int *cb0,
+                                           u64 *ck1, int *ca1, int *cb1, int *comp, u64 *best0, u64 *best1, u64 *er,
+                                           long long er_cap) {
+    const long long T = ONE ? (long long)threadIdx.x : gtid();
+    const long long S = ONE ? (long long)blockDim.x : gstride();
+    const long long B0 = ONE ? 0 : (long long)blockIdx.x * blockDim.x;
     for (;; ++r) {
         if (r >= MAX_ROUNDS) {
-            if (gtid() == 0) atomicOr(&ctl->err, ERR_ROUNDS);
-            return;
+            if (T == 0) atomicOr(&ctl->err, ERR_ROUNDS);
+            return 0;
         }
         u64 *ck = (r & 1) ? ck1 : ck0, *ckn = (r & 1) ? ck0 : ck1;
         int *ca = (r & 1) ? ca1 : ca0, *can = (r & 1) ? ca0 : ca1;
         int *cb = (r & 1) ? cb1 : cb0, *cbn = (r & 1) ? cb0 : cb1;
         u64 *best = (r & 1) ? best1 : best0, *bestn = (r & 1) ? best0 : best1;
-        long long c = r == 0 ? c0 : (long long)*(volatile u64 *)&ctl->cnt[r % 3];
-        if (gtid() == 0) {
+        const long long c = r == 0 ? c0 : (long long)*(volatile u64 *)&ctl->cnt[r % 3];
+        if (!ONE && r > 0 && c <= HOOK_TAIL) return r;
+        if (T == 0) {
             ctl->cnt[(r + 2) % 3] = 0;
             ctl->flag[(r + 1) % 3] = 0;
         }
         // phase A: roots of both ends, per-component minimum key
-        for (long long i = gtid(); i < c; i += gstride()) {
+        for (long long i = T; i < c; i += S) {
             int a = LD(ca[i]), b = LD(cb[i]);
             if (r > 0) {   // every endpoint is its own root in round 0
                 a = find_root_ro(comp, a, ctl);
@@ -976,11 +969,11 @@ __global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int 
             hm_min(hm, best, b, k, a != b);
         }
         hm_flush(hm, best, bestn);
-        if (!grid_barrier(ctl, &ctl->bar[1])) return;
+        if (!ONE && !grid_barrier(ctl, &ctl->bar[1])) return -1;
         // phase B: hook along minimum edges, keep the rest (block-uniform
         // loop: list appends are reserved once per block)
         bool hooked = false;
-        for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < c; b0 += gstride()) {
+        for (long long b0 = B0; b0 < c; b0 += S) {
             const long long i = b0 + threadIdx.x;
             int a = 0, b = 0;
             bool alive = false, hook = false, keep = false;
@@ -1015,11 +1008,47 @@ __global__ void k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int 
             }
         }
         hm_flush(hm, best, bestn);
-        if (__syncthreads_or(hooked) && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
-        if (!grid_barrier(ctl, &ctl->bar[1])) return;
-        if (!*(volatile int *)&ctl->flag[r % 3]) break;
+        const int any = __syncthreads_or(hooked);
+        if (ONE) {
+            if (!any) break;
+        } else {
+            if (any && threadIdx.x == 0) atomicOr(&ctl->flag[r % 3], 1);
+            if (!grid_barrier(ctl, &ctl->bar[1])) return -1;
+            if (!*(volatile int *)&ctl->flag[r % 3]) break;
+        }
     }
-    if (gtid() == 0) ctl->hook_rounds = r;
+    if (T == 0) ctl->hook_rounds = r;
+    return 0;
+}
+
+__global__ void __launch_bounds__(HOOK_THREADS, 1) k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1,
+                                                          int *ca1, int *cb1, HookSlots hs, u64 *er,
+                                                          long long er_cap, int init) {
+    if (*(volatile int *)&ctl->skip) return;
+    __shared__ HotMin hm;
+    const unsigned ep = ctl->epoch;
+    const long long c0 = (long long)ctl->ncand;
+    if (gtid() == 0) {
+        ctl->cnt[1] = ctl->cnt[2] = 0;
+        ctl->flag[0] = ctl->flag[1] = ctl->flag[2] = 0;
+    }
+    hm_init(hm);
+    if (init) {
+        // set up each candidate endpoint once (the first lane to stamp it);
+        // with init == 0 the kernel that wrote the candidates did it and
+        // round 0 starts at once
+        for (long long i = gtid(); i < c0; i += gstride()) {
+            hook_slot_init(hs, ca0[i], ep);
+            hook_slot_init(hs, cb0[i], ep);
+        }
+        if (!grid_barrier(ctl, &ctl->bar[1])) return;
+    } else {
+        __syncthreads();
+    }
+    const int r = hook_rounds<false>(ctl, hm, 0, c0, ck0, ca0, cb0, ck1, ca1, cb1, hs.comp, hs.best0, hs.best1, er,
+                                     er_cap);
+    if (r > 0 && blockIdx.x == 0)
+        hook_rounds<true>(ctl, hm, r, c0, ck0, ca0, cb0, ck1, ca1, cb1, hs.comp, hs.best0, hs.best1, er, er_cap);
 }
 
 // Orientation of replacement edge i: down = its lower-id endpoint's piece
@@ -1635,7 +1664,14 @@ unsigned coop_blocks_jump(int nsm) {
              c = coop_blocks((const void *)k_jump<2>, nsm, 8);
     return a < b ? (a < c ? a : c) : (b < c ? b : c);
 }
-unsigned coop_blocks_hook(int nsm) { return coop_blocks((const void *)k_boruvka, nsm, 4); }
+unsigned coop_blocks_hook(int nsm) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k_boruvka, HOOK_THREADS, 0) != cudaSuccess ||
+        per < 1)
+        per = 1;
+    if (per > 1) per = 1;
+    return (unsigned)(per * nsm);
+}
 unsigned coop_blocks_orient(int nsm) {
     cudaFuncSetAttribute((const void *)k_orient, cudaFuncAttributeMaxDynamicSharedMemorySize, ORIENT_SMEM_BYTES);
     int per = 0;
@@ -1694,7 +1730,7 @@ cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0,
                            HookSlots hs, u64 *er, long long er_cap, int init, cudaStream_t s) {
     void *args[] = {(void *)&ctl, (void *)&ck0, (void *)&ca0, (void *)&cb0, (void *)&ck1, (void *)&ca1,
                     (void *)&cb1, (void *)&hs, (void *)&er, (void *)&er_cap, (void *)&init};
-    return cudaLaunchCooperativeKernel((const void *)k_boruvka, d.coop_hook, BLK, args, 0, s);
+    return cudaLaunchCooperativeKernel((const void *)k_boruvka, d.coop_hook, HOOK_THREADS, args, 0, s);
 }
 cudaError_t launch_orient(const Dev &d, Ctl *ctl, OrientArgs a, cudaStream_t s) {
     void *args[] = {(void *)&ctl, (void *)&a};
