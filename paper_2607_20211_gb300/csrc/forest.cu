@@ -23,7 +23,9 @@
 #define ORIENT_THREADS 1024
 // hooking: threads per block (one block per SM) and the live candidates at
 // the start of a round (after round 0) up to which block 0 finishes alone
+#ifndef HOOK_THREADS
 #define HOOK_THREADS 1024
+#endif
 #define HOOK_TAIL 8192
 // a core of at most this many edges is oriented by one block (measured on
 // R-MAT-22: faster than the grid phases for small batches' cores of tens of
@@ -1021,7 +1023,7 @@ __device__ __forceinline__ int hook_rounds(Ctl *ctl, HotMin &hm, int r, long lon
     return 0;
 }
 
-__global__ void __launch_bounds__(HOOK_THREADS, 1) k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1,
+__global__ void __launch_bounds__(HOOK_THREADS, 1024 / HOOK_THREADS) k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1,
                                                           int *ca1, int *cb1, HookSlots hs, u64 *er,
                                                           long long er_cap, int init) {
     if (*(volatile int *)&ctl->skip) return;
@@ -1669,7 +1671,7 @@ unsigned coop_blocks_hook(int nsm) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k_boruvka, HOOK_THREADS, 0) != cudaSuccess ||
         per < 1)
         per = 1;
-    if (per > 1) per = 1;
+    if (per > 1024 / HOOK_THREADS) per = 1024 / HOOK_THREADS;
     return (unsigned)(per * nsm);
 }
 unsigned coop_blocks_orient(int nsm) {
