@@ -624,6 +624,7 @@ drsf_status drsf_create(int32_t n, const int32_t *edges, int64_t m, const int32_
     h->dev.grid = (unsigned)nsm * 8u;
     h->dev.coop_jump = coop_blocks_jump(nsm);
     h->dev.coop_hook = coop_blocks_hook(nsm);
+    h->dev.coop_hook_small = coop_blocks_hook_small(nsm);
     h->dev.coop_orient = coop_blocks_orient(nsm);
     h->dev.coop_mark = coop_blocks_mark(nsm);
     h->dev.coop_bfs = coop_blocks_bfs(nsm);
@@ -729,7 +730,7 @@ static drsf_status launch_rest(drsf_ctx *h, int op, bool sg, long long glen, cud
     // their hook-forest slots; otherwise the hooking sets them up itself
     // (inside the scan of a large delete that costs more than it saves)
     CK(launch_boruvka(h->dev, ctl, h->ck[0], h->ca[0], h->cb[0], h->ck[1], h->ca[1], h->cb[1], hook_slots(h), h->er,
-                      h->n, (op == DRSF_INSERT && !sg) ? 0 : 1, s));
+                      h->n, (op == DRSF_INSERT && !sg) ? 0 : 1, glen > (1 << 18), s));
     prof_end(h, PH_HOOK, 1, s);
     OrientArgs oa{};
     oa.er = h->er;

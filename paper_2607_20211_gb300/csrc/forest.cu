@@ -23,9 +23,10 @@
 #define ORIENT_THREADS 1024
 // hooking: threads per block (one block per SM) and the live candidates at
 // the start of a round (after round 0) up to which block 0 finishes alone
-#ifndef HOOK_THREADS
-#define HOOK_THREADS 1024
-#endif
+// (the kernel comes in two block sizes: 1024 threads, one block per SM, so
+// that block 0 has the threads for the tail, and 256 threads, four per SM,
+// for batches whose candidates stay in the millions past round 0, where
+// the grid rounds measured faster with smaller blocks)
 #define HOOK_TAIL 8192
 // a core of at most this many edges is oriented by one block (measured on
 // R-MAT-22: faster than the grid phases for small batches' cores of tens of
@@ -1023,7 +1024,8 @@ __device__ __forceinline__ int hook_rounds(Ctl *ctl, HotMin &hm, int r, long lon
     return 0;
 }
 
-__global__ void __launch_bounds__(HOOK_THREADS, 1024 / HOOK_THREADS) k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1,
+template <int HT>
+__global__ void __launch_bounds__(HT, 1024 / HT) k_boruvka(Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1,
                                                           int *ca1, int *cb1, HookSlots hs, u64 *er,
                                                           long long er_cap, int init) {
     if (*(volatile int *)&ctl->skip) return;
@@ -1666,14 +1668,14 @@ unsigned coop_blocks_jump(int nsm) {
              c = coop_blocks((const void *)k_jump<2>, nsm, 8);
     return a < b ? (a < c ? a : c) : (b < c ? b : c);
 }
-unsigned coop_blocks_hook(int nsm) {
+static unsigned coop_blocks_hook_t(const void *fn, int threads, int nsm) {
     int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k_boruvka, HOOK_THREADS, 0) != cudaSuccess ||
-        per < 1)
-        per = 1;
-    if (per > 1024 / HOOK_THREADS) per = 1024 / HOOK_THREADS;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0) != cudaSuccess || per < 1) per = 1;
+    if (per > 1024 / threads) per = 1024 / threads;
     return (unsigned)(per * nsm);
 }
+unsigned coop_blocks_hook(int nsm) { return coop_blocks_hook_t((const void *)k_boruvka<1024>, 1024, nsm); }
+unsigned coop_blocks_hook_small(int nsm) { return coop_blocks_hook_t((const void *)k_boruvka<256>, 256, nsm); }
 unsigned coop_blocks_orient(int nsm) {
     cudaFuncSetAttribute((const void *)k_orient, cudaFuncAttributeMaxDynamicSharedMemorySize, ORIENT_SMEM_BYTES);
     int per = 0;
@@ -1729,10 +1731,12 @@ cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_
     return cudaLaunchCooperativeKernel(fn, d.coop_jump, BLK, args, 0, s);
 }
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
-                           HookSlots hs, u64 *er, long long er_cap, int init, cudaStream_t s) {
+                           HookSlots hs, u64 *er, long long er_cap, int init, bool large, cudaStream_t s) {
     void *args[] = {(void *)&ctl, (void *)&ck0, (void *)&ca0, (void *)&cb0, (void *)&ck1, (void *)&ca1,
                     (void *)&cb1, (void *)&hs, (void *)&er, (void *)&er_cap, (void *)&init};
-    return cudaLaunchCooperativeKernel((const void *)k_boruvka, d.coop_hook, HOOK_THREADS, args, 0, s);
+    if (large)
+        return cudaLaunchCooperativeKernel((const void *)k_boruvka<256>, d.coop_hook_small, 256, args, 0, s);
+    return cudaLaunchCooperativeKernel((const void *)k_boruvka<1024>, d.coop_hook, 1024, args, 0, s);
 }
 cudaError_t launch_orient(const Dev &d, Ctl *ctl, OrientArgs a, cudaStream_t s) {
     void *args[] = {(void *)&ctl, (void *)&a};

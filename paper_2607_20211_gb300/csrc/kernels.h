@@ -11,7 +11,8 @@ struct Dev {
     int nsm;
     unsigned grid;        // grid-stride kernels: nsm * 8 blocks of BLK
     unsigned coop_jump;   // cooperative kernels: co-resident block counts
-    unsigned coop_hook;
+    unsigned coop_hook;        // (1024-thread blocks)
+    unsigned coop_hook_small;  // (256-thread blocks, for large batches)
     unsigned coop_orient;
     unsigned coop_mark;
     unsigned coop_bfs;
@@ -95,9 +96,10 @@ cudaError_t launch_jump_async(const Dev &d, const int *A, Ctl *ctl, int *J, int 
 cudaError_t launch_jump(const Dev &d, const int *A, int use_list, long long cnt_static, Ctl *ctl, const int *par,
                         int *J, int *J1, int *rep, RowList rl, int mode, const int *rold, unsigned *w, u64 *heavy,
                         Csr g, int sync_rounds, int *X, int *Y, const int *cuts, cudaStream_t s);
-// init: set up the candidates' endpoints first (0: their writer did, HookSlots)
+// init: set up the candidates' endpoints first (0: their writer did, HookSlots);
+// large: a batch whose candidates stay many past round 0 (smaller blocks)
 cudaError_t launch_boruvka(const Dev &d, Ctl *ctl, u64 *ck0, int *ca0, int *cb0, u64 *ck1, int *ca1, int *cb1,
-                           HookSlots hs, u64 *er, long long er_cap, int init, cudaStream_t s);
+                           HookSlots hs, u64 *er, long long er_cap, int init, bool large, cudaStream_t s);
 struct OrientArgs {
     const u64 *er;
     const int *rep;
@@ -134,6 +136,7 @@ unsigned coop_blocks_jump(int nsm);
 unsigned grid_vertex_pass(int nsm);
 unsigned grid_list_pass(int nsm);
 unsigned coop_blocks_hook(int nsm);
+unsigned coop_blocks_hook_small(int nsm);
 unsigned coop_blocks_orient(int nsm);
 unsigned coop_blocks_mark(int nsm);
 cudaError_t launch_barrier_selftest(Ctl *ctl, cudaStream_t s);
