@@ -681,7 +681,7 @@ static bool use_supergraph(const drsf_ctx *h, int op, long long len) {
 static drsf_status launch_rest(drsf_ctx *h, int op, bool sg, long long glen, cudaStream_t s) {
     Ctl *ctl = h->ctl;
     Csr g{h->off, h->used, h->col};
-    CK(launch_validate_batch(glen, h->n, ctl, h->rep, h->parent, h->off, s));
+    CK(launch_validate_batch(glen, h->n, ctl, s));
     prof_end(h, PH_BEGIN, 2, s);
     if (op == DRSF_INSERT) {
         // Algorithm 1, insert: F^ = F, M = B; rep of the previous batch is current

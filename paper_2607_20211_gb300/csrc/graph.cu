@@ -150,12 +150,8 @@ __global__ void k_fill(const u64 *dkey, const u64 *dslot, long long m, Csr g, In
 
 // ------------------------------------------------------------ per batch
 
-// Id validation of the batch.  A batch that touches a notable share of the
-// vertices (at least one per 64) also pulls the per-vertex arrays that the
-// next kernel gathers from at random into L2: rep (both operations) and the
-// parent array (delete) or the row offsets (insert), when they fit in L2
-// with room to spare (on larger graphs they would only evict one another).
-__global__ void k_validate_batch(int n, Ctl *ctl, const int *rep, const int *parent, const long long *off) {
+// Id validation of the batch: an out-of-range id skips the whole batch.
+__global__ void k_validate_batch(int n, Ctl *ctl) {
     const int *batch = ctl->batch;
     const long long len = ctl->batch_len;
     GS_LOOP(i, 2 * len) {
@@ -164,12 +160,6 @@ __global__ void k_validate_batch(int n, Ctl *ctl, const int *rep, const int *par
             atomicOr(&ctl->err, ERR_BATCH_ID);
             ctl->skip = 1;
         }
-    }
-    if (len * 64 >= n && n <= (1 << 23)) {   // (two arrays of at most 32 MB: well inside L2)
-        const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
-        l2_prefetch(rep, 4ll * n, t, nt);
-        if (ctl->op == 1) l2_prefetch(parent, 4ll * n, t, nt);
-        else l2_prefetch(off, 8ll * (n + 1), t, nt);
     }
 }
 
@@ -640,9 +630,8 @@ cudaError_t launch_fill(const u64 *dkey, const u64 *dslot, long long m, Csr g, I
 }
 // The batch kernels read the batch and its length from the control block;
 // `len` only sizes their grid (a captured launch sequence is keyed by it).
-cudaError_t launch_validate_batch(long long len, int n, Ctl *ctl, const int *rep, const int *parent,
-                                  const long long *off, cudaStream_t s) {
-    k_validate_batch<<<gsz(2 * len), BLK, 0, s>>>(n, ctl, rep, parent, off);
+cudaError_t launch_validate_batch(long long len, int n, Ctl *ctl, cudaStream_t s) {
+    k_validate_batch<<<gsz(2 * len), BLK, 0, s>>>(n, ctl);
     return cudaGetLastError();
 }
 cudaError_t launch_ins_claim(long long len, Index ix, Ctl *ctl, u64 *nkey, u64 *nslot, cudaStream_t s) {

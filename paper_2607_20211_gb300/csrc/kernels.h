@@ -33,8 +33,7 @@ cudaError_t launch_caps(const int *deg, int n, long long *cap, cudaStream_t s);
 cudaError_t launch_scan_i64(const long long *in, long long *out, long long n, long long *bsum, cudaStream_t s);
 cudaError_t launch_fill(const u64 *dkey, const u64 *dslot, long long m, Csr g, Index ix, cudaStream_t s);
 // (the batch kernels read the batch from the control block; len sizes the grid)
-cudaError_t launch_validate_batch(long long len, int n, Ctl *ctl, const int *rep, const int *parent,
-                                  const long long *off, cudaStream_t s);
+cudaError_t launch_validate_batch(long long len, int n, Ctl *ctl, cudaStream_t s);
 
 cudaError_t launch_del_claim(long long len, Index ix, Csr g, u64 *ovf, int *parent, const int *rep, Ctl *ctl,
                              unsigned *aff_ep, unsigned *cut_ep, int *cutlist, unsigned *w, int *rold,
